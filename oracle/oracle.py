@@ -1,0 +1,209 @@
+"""ctypes wrapper of the C oracle (orc.c).
+
+TEST INFRASTRUCTURE ONLY: used by the tests, the smoke check and the
+benchmark's CPU-baseline leg to check and time the CUDA library. The product
+path never imports this module.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+SRC = os.path.join(HERE, "orc.c")
+HDR = os.path.join(HERE, "orc.h")
+LIB = os.path.join(HERE, "_build", "liborc.so")
+
+OK, ERR_ARG, ERR_GEOM, ERR_NEG_MEAN, ERR_NONFINITE = 0, -1, -2, -3, -4
+
+
+def build(force: bool = False) -> str:
+    """Compile orc.c into _build/liborc.so (gcc, OpenMP, no FMA contraction so
+    that results agree between x86-64 and aarch64 hosts)."""
+    os.makedirs(os.path.dirname(LIB), exist_ok=True)
+    stale = (not os.path.exists(LIB) or
+             os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
+    if force or stale:
+        tmp = LIB + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
+               "-o", tmp, SRC, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, LIB)
+    return LIB
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("flux", ctypes.c_int), ("av", ctypes.c_int), ("eps0", ctypes.c_double),
+                ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
+                ("limiter", ctypes.c_int), ("h_tol", ctypes.c_double), ("rk", ctypes.c_int),
+                ("cfl", ctypes.c_double)]
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        _lib = ctypes.CDLL(build())
+        dp = ctypes.POINTER(ctypes.c_double)
+        ip = ctypes.POINTER(ctypes.c_int)
+        vp = ctypes.c_void_p
+        L = _lib
+        L.orc_basis.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
+        L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ip, ip, ip, dp, ctypes.c_double,
+                                 ctypes.POINTER(Params), ctypes.POINTER(vp)]
+        L.orc_destroy.argtypes = [vp]
+        L.orc_destroy.restype = None
+        L.orc_geometry.argtypes = [vp, dp, dp, dp, dp, dp]
+        L.orc_rhs.argtypes = [vp, dp, dp]
+        L.orc_get_epsilon.argtypes = [vp, dp]
+        L.orc_av_fields.argtypes = [vp, dp, dp, dp]
+        L.orc_limit.argtypes = [vp, dp]
+        L.orc_max_dt.argtypes = [vp, dp, dp, dp]
+        L.orc_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, dp]
+        L.orc_mass.argtypes = [vp, dp, dp]
+        L.orc_entropy.argtypes = [vp, dp, dp]
+        L.orc_volume_flux.argtypes = [ctypes.c_double, dp, dp, dp, dp]
+        L.orc_volume_flux.restype = None
+        L.orc_surface_flux.argtypes = [ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
+        L.orc_surface_flux.restype = None
+        L.orc_threads.argtypes = []
+        L.orc_lsrk_coefficients.argtypes = [dp, dp]
+        L.orc_lsrk_coefficients.restype = None
+    return _lib
+
+
+def _p(a: np.ndarray):
+    assert a.flags["C_CONTIGUOUS"]
+    if a.dtype == np.float64:
+        return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    assert a.dtype == np.int32
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_int))
+
+
+def basis(N: int):
+    n = N + 1
+    xi, w = np.zeros(n), np.zeros(n)
+    D, V, Vinv = np.zeros((n, n)), np.zeros((n, n)), np.zeros((n, n))
+    rc = lib().orc_basis(N, _p(xi), _p(w), _p(D), _p(V), _p(Vinv))
+    if rc:
+        raise ValueError(f"orc_basis rc={rc}")
+    return xi, w, D, V, Vinv
+
+
+def volume_flux(g, Wa, Wb):
+    Fs, Gs = np.zeros(3), np.zeros(3)
+    lib().orc_volume_flux(g, _p(np.ascontiguousarray(Wa, dtype=np.float64)),
+                          _p(np.ascontiguousarray(Wb, dtype=np.float64)), _p(Fs), _p(Gs))
+    return Fs, Gs
+
+
+def surface_flux(g, es, Wm, Wp, bm, bp, nx, ny):
+    F = np.zeros(3)
+    lib().orc_surface_flux(g, int(es), _p(np.ascontiguousarray(Wm, dtype=np.float64)),
+                           _p(np.ascontiguousarray(Wp, dtype=np.float64)), bm, bp, nx, ny, _p(F))
+    return F
+
+
+def lsrk_coefficients():
+    A, B = np.zeros(5), np.zeros(5)
+    lib().orc_lsrk_coefficients(_p(A), _p(B))
+    return A, B
+
+
+def threads() -> int:
+    return lib().orc_threads()
+
+
+class Oracle:
+    """Oracle instance for one Problem (see paper_1804_02221_gb300.inputs)."""
+
+    def __init__(self, prob, flux=1, av=False, eps0=0.0, sigma_min=math.nan, sigma_max=math.nan,
+                 limiter=False, h_tol=math.nan, rk=0, cfl=0.5):
+        self.prob = prob
+        self.N, self.K, self.n = prob.N, prob.K, prob.N + 1
+        self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
+                             int(limiter), float(h_tol), int(rk), float(cfl))
+        self._x = np.ascontiguousarray(prob.x, dtype=np.float64)
+        self._y = np.ascontiguousarray(prob.y, dtype=np.float64)
+        self._b = np.ascontiguousarray(prob.b, dtype=np.float64)
+        self._E = np.ascontiguousarray(prob.EToE, dtype=np.int32)
+        self._F = np.ascontiguousarray(prob.EToF, dtype=np.int32)
+        self._fl = np.ascontiguousarray(prob.flip, dtype=np.int32)
+        h = ctypes.c_void_p()
+        rc = lib().orc_create(self.N, self.K, _p(self._x), _p(self._y), _p(self._E), _p(self._F),
+                              _p(self._fl), _p(self._b), float(prob.g), ctypes.byref(self.params),
+                              ctypes.byref(h))
+        if rc:
+            raise ValueError(f"orc_create rc={rc}")
+        self._h = h
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value and _lib is not None:
+            _lib.orc_destroy(h)
+            self._h = None
+
+    def _W(self, W):
+        W = np.ascontiguousarray(W, dtype=np.float64)
+        assert W.shape == (3, self.K, self.n, self.n), W.shape
+        return W
+
+    def geometry(self):
+        shp = (self.K, self.n, self.n)
+        out = [np.zeros(shp) for _ in range(5)]
+        lib().orc_geometry(self._h, *[_p(a) for a in out])
+        return dict(zip(("x_xi", "x_eta", "y_xi", "y_eta", "J"), out))
+
+    def rhs(self, W):
+        W = self._W(W)
+        R = np.zeros_like(W)
+        rc = lib().orc_rhs(self._h, _p(W), _p(R))
+        if rc:
+            raise RuntimeError(f"orc_rhs rc={rc}")
+        return R
+
+    def epsilon(self):
+        e = np.zeros(self.K)
+        lib().orc_get_epsilon(self._h, _p(e))
+        return e
+
+    def av_fields(self, W):
+        W = self._W(W)
+        eps = np.zeros(self.K)
+        grads = np.zeros((4, self.K, self.n, self.n))
+        lib().orc_av_fields(self._h, _p(W), _p(eps), _p(grads))
+        return eps, grads
+
+    def limit(self, W):
+        W = self._W(W).copy()
+        rc = lib().orc_limit(self._h, _p(W))
+        return W, rc
+
+    def max_dt(self, W):
+        W = self._W(W)
+        dc, dp = ctypes.c_double(), ctypes.c_double()
+        lib().orc_max_dt(self._h, _p(W), ctypes.byref(dc), ctypes.byref(dp))
+        return dc.value, dp.value
+
+    def step(self, W, dt=0.0, nsteps=1):
+        W = self._W(W).copy()
+        dl = ctypes.c_double(0.0)
+        rc = lib().orc_step(self._h, _p(W), float(dt), int(nsteps), ctypes.byref(dl))
+        return W, rc, dl.value
+
+    def mass(self, W):
+        out = np.zeros(3)
+        lib().orc_mass(self._h, _p(self._W(W)), _p(out))
+        return out
+
+    def entropy(self, W):
+        e = ctypes.c_double()
+        lib().orc_entropy(self._h, _p(self._W(W)), ctypes.byref(e))
+        return e.value

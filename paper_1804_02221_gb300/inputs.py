@@ -1,0 +1,332 @@
+"""Seeded synthetic inputs: meshes, bathymetries and initial states.
+
+This module holds none of the scheme's arithmetic. It evaluates analytic
+mappings and fields at Legendre-Gauss-Lobatto positions (taken from numpy's
+Legendre-polynomial roots) and builds periodic quadrilateral connectivity.
+Both the CUDA library's tests and the oracle's tests draw their inputs here.
+
+Array layout (shared with the library's C-ABI):
+  x, y, b          float64 [K, n, n]     index [k, j, i], i along xi (fastest)
+  W                float64 [3, K, n, n]  (h, hu, hv)
+  EToE, EToF, flip int32   [K, 4]        faces 0: eta=-1, 1: xi=+1, 2: eta=+1, 3: xi=-1
+
+Face node p runs along increasing xi (faces 0, 2) or eta (faces 1, 3); node p of
+face (k, f) meets node (N - p if flip else p) of face (EToE[k, f], EToF[k, f]).
+"""
+from __future__ import annotations
+
+import dataclasses
+import math
+
+import numpy as np
+
+
+def lgl_points(N: int) -> np.ndarray:
+    """LGL positions -1, roots of L_N', +1 (numpy polynomial root finder)."""
+    if N < 1:
+        raise ValueError("N >= 1 required")
+    inner = np.polynomial.legendre.Legendre.basis(N).deriv().roots()
+    return np.concatenate(([-1.0], np.sort(np.real(inner)), [1.0]))
+
+
+@dataclasses.dataclass
+class Problem:
+    """One synthetic instance: mesh, bathymetry, gravity and initial state."""
+
+    name: str
+    N: int
+    Kx: int
+    Ky: int
+    x: np.ndarray
+    y: np.ndarray
+    b: np.ndarray
+    W: np.ndarray
+    EToE: np.ndarray
+    EToF: np.ndarray
+    flip: np.ndarray
+    g: float = 9.81
+    meta: dict = dataclasses.field(default_factory=dict)
+
+    @property
+    def K(self) -> int:
+        return self.x.shape[0]
+
+    @property
+    def n(self) -> int:
+        return self.N + 1
+
+    @property
+    def nodes(self) -> int:
+        return self.K * self.n * self.n
+
+
+# ---------------------------------------------------------------------------
+# Mesh: periodic structured quads, optionally with rotated element frames
+# ---------------------------------------------------------------------------
+
+def _local_to_canonical(N: int, r: int, ii: np.ndarray, jj: np.ndarray):
+    """Canonical node (i, j) of local node (ii, jj) of an element whose local
+    frame is rotated by r quarter turns."""
+    if r == 0:
+        return ii, jj
+    if r == 1:
+        return N - jj, ii
+    if r == 2:
+        return N - ii, N - jj
+    return jj, N - ii
+
+
+def _face_local_nodes(N: int, f: int):
+    p = np.arange(N + 1)
+    if f == 0:
+        return p, np.zeros_like(p)
+    if f == 1:
+        return np.full_like(p, N), p
+    if f == 2:
+        return p, np.full_like(p, N)
+    return np.zeros_like(p), p
+
+
+def _canonical_face_of(N: int, i: np.ndarray, j: np.ndarray) -> int:
+    if np.all(j == 0):
+        return 0
+    if np.all(i == N):
+        return 1
+    if np.all(j == N):
+        return 2
+    return 3
+
+
+def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None):
+    """Periodic Kx x Ky quad mesh of the box domain=(x0, x1, y0, y1).
+
+    ``mapping(X, Y)`` returns the displacement (dx, dy) of the lattice point
+    (X, Y) given in wrapped coordinates; it must be periodic. Returns
+    (x, y, xw, yw, EToE, EToF, flip) where (xw, yw) are the physical
+    coordinates wrapped into the periodic box (identical bit patterns on both
+    sides of every face, so fields evaluated there agree across faces).
+    """
+    x0, x1, y0, y1 = domain
+    Lx, Ly = x1 - x0, y1 - y0
+    n = N + 1
+    r = lgl_points(N)
+    K = Kx * Ky
+    rng = np.random.default_rng(rotate_seed) if rotate_seed is not None else None
+    rot = rng.integers(0, 4, size=K) if rng is not None else np.zeros(K, dtype=np.int64)
+
+    # canonical lattice coordinates (exact at element corners)
+    ex = np.arange(Kx)[:, None] + (r[None, :] + 1.0) / 2.0  # [Kx, n]
+    ey = np.arange(Ky)[:, None] + (r[None, :] + 1.0) / 2.0
+    Xc = x0 + Lx * ex / Kx
+    Yc = y0 + Ly * ey / Ky
+    Xcw = np.where(Xc >= x1, Xc - Lx, Xc)
+    Ycw = np.where(Yc >= y1, Yc - Ly, Yc)
+
+    x = np.empty((K, n, n))
+    y = np.empty((K, n, n))
+    xw = np.empty((K, n, n))
+    yw = np.empty((K, n, n))
+    jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")  # [j, i]
+    for ky in range(Ky):
+        for kx in range(Kx):
+            k = ky * Kx + kx
+            ci, cj = _local_to_canonical(N, int(rot[k]), ii, jj)
+            X, Y = Xc[kx][ci], Yc[ky][cj]
+            XW, YW = Xcw[kx][ci], Ycw[ky][cj]
+            dx, dy = mapping(XW, YW)
+            x[k] = X + dx
+            y[k] = Y + dy
+            xw[k] = XW + dx
+            yw[k] = YW + dy
+
+    EToE = np.empty((K, 4), dtype=np.int32)
+    EToF = np.empty((K, 4), dtype=np.int32)
+    flip = np.empty((K, 4), dtype=np.int32)
+    # local face -> canonical face, and whether the local node order runs
+    # against the canonical order along that face
+    canon = np.empty((K, 4), dtype=np.int64)
+    rev = np.empty((K, 4), dtype=bool)
+    for k in range(K):
+        for f in range(4):
+            li, lj = _face_local_nodes(N, f)
+            ci, cj = _local_to_canonical(N, int(rot[k]), li, lj)
+            F = _canonical_face_of(N, ci, cj)
+            canon[k, f] = F
+            pos = ci if F in (0, 2) else cj
+            rev[k, f] = pos[0] == N
+    local_of = {}
+    for k in range(K):
+        for f in range(4):
+            local_of[(k, int(canon[k, f]))] = f
+    for ky in range(Ky):
+        for kx in range(Kx):
+            k = ky * Kx + kx
+            for f in range(4):
+                F = int(canon[k, f])
+                if F == 0:
+                    nb = ((ky - 1) % Ky) * Kx + kx
+                elif F == 1:
+                    nb = ky * Kx + (kx + 1) % Kx
+                elif F == 2:
+                    nb = ((ky + 1) % Ky) * Kx + kx
+                else:
+                    nb = ky * Kx + (kx - 1) % Kx
+                Fn = (F + 2) % 4
+                fn = local_of[(nb, Fn)]
+                EToE[k, f] = nb
+                EToF[k, f] = fn
+                flip[k, f] = int(rev[k, f] != rev[nb, fn])
+    return x, y, xw, yw, EToE, EToF, flip
+
+
+# ---------------------------------------------------------------------------
+# Mappings and fields
+# ---------------------------------------------------------------------------
+
+def _sine_map(amp: float, freq: float):
+    def mapping(X, Y):
+        d = amp * np.sin(freq * X) * np.sin(freq * Y)
+        return d, d
+    return mapping
+
+
+def _gaussian_sum_periodic(xw, yw, a, c, s, Lx, Ly):
+    B = np.zeros_like(xw)
+    for ak, ck, sk in zip(a, c, s):
+        for sx in (-Lx, 0.0, Lx):
+            for sy in (-Ly, 0.0, Ly):
+                B += ak * np.exp(-((xw - ck[0] - sx) ** 2 + (yw - ck[1] - sy) ** 2) / sk ** 2)
+    return B
+
+
+def _smooth_periodic_field(rng, xw, yw, Lx, Ly, modes=3):
+    """Random smooth periodic field of unit-order amplitude."""
+    f = np.zeros_like(xw)
+    for p in range(modes + 1):
+        for q in range(modes + 1):
+            a, bb, c, d = rng.standard_normal(4) / (1.0 + p * p + q * q)
+            kx, ky = 2 * math.pi * p / Lx, 2 * math.pi * q / Ly
+            f += a * np.cos(kx * xw) * np.cos(ky * yw) + bb * np.sin(kx * xw) * np.cos(ky * yw)
+            f += c * np.cos(kx * xw) * np.sin(ky * yw) + d * np.sin(kx * xw) * np.sin(ky * yw)
+    return f / max(1e-300, np.max(np.abs(f)))
+
+
+def _state(h, u, v):
+    return np.ascontiguousarray(np.stack([h, h * u, h * v]))
+
+
+def lake_hump(N=3, K1=8, seed=0, rotate_seed=None, g=9.81, amp=0.01) -> Problem:
+    """Lake at rest h+b=1 on b=0.1+0.05 sin(pi x)cos(pi y) plus a seeded
+    Gaussian hump (amplitude 0.01, width 0.2) on the curved periodic
+    [0,2]^2 mesh x += 0.05 sin(pi x) sin(pi y) (same for y)."""
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, K1, K1, (0.0, 2.0, 0.0, 2.0),
+                                           _sine_map(0.05, math.pi), rotate_seed)
+    rng = np.random.default_rng(seed)
+    c0 = rng.uniform(0.5, 1.5, size=2)
+    b = 0.1 + 0.05 * np.sin(math.pi * xw) * np.cos(math.pi * yw)
+    h = 1.0 - b + amp * np.exp(-((xw - c0[0]) ** 2 + (yw - c0[1]) ** 2) / 0.2 ** 2)
+    z = np.zeros_like(h)
+    return Problem("lake_hump", N, K1, K1, x, y, b, _state(h, z, z), E, F, fl, g,
+                   {"hump_center": c0.tolist()})
+
+
+def lake_at_rest_kinked(N=3, K1=6, rotate_seed=None, g=9.81, H=1.0) -> Problem:
+    """h+b=H, u=v=0 on the curved [0,2]^2 mesh with b continuous but not
+    smooth: the lake_hump bathymetry plus a cone 0.1 max(0, 1 - r/0.5)."""
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, K1, K1, (0.0, 2.0, 0.0, 2.0),
+                                           _sine_map(0.05, math.pi), rotate_seed)
+    r = np.sqrt((xw - 0.93) ** 2 + (yw - 1.07) ** 2)
+    b = 0.1 + 0.05 * np.sin(math.pi * xw) * np.cos(math.pi * yw) + 0.1 * np.maximum(0.0, 1.0 - r / 0.5)
+    h = H - b
+    z = np.zeros_like(h)
+    return Problem("lake_at_rest_kinked", N, K1, K1, x, y, b, _state(h, z, z), E, F, fl, g)
+
+
+def dam_break(N=7, K1=None, seed=1, rotate_seed=None, g=9.81) -> Problem:
+    """Degree-sweep workload: periodic curved [0,2]^2 mesh with K1 x K1 quads
+    (default round(2048/(N+1)), about 4.2M nodes), bathymetry 0.3 B/max B with
+    B a sum of 8 seeded Gaussians (periodic images), total height H = 2.0
+    where x < 1 + 0.25 sin(pi y) and 0.5 elsewhere, at rest."""
+    if K1 is None:
+        K1 = int(round(2048 / (N + 1)))
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, K1, K1, (0.0, 2.0, 0.0, 2.0),
+                                           _sine_map(0.05, math.pi), rotate_seed)
+    rng = np.random.default_rng(seed)
+    a = rng.uniform(0.2, 1.0, size=8)
+    c = rng.uniform(0.0, 2.0, size=(8, 2))
+    s = rng.uniform(0.1, 0.4, size=8)
+    B = _gaussian_sum_periodic(xw, yw, a, c, s, 2.0, 2.0)
+    b = 0.3 * B / B.max()
+    H = np.where(xw < 1.0 + 0.25 * np.sin(math.pi * yw), 2.0, 0.5)
+    h = H - b
+    z = np.zeros_like(h)
+    return Problem("dam_break", N, K1, K1, x, y, b, _state(h, z, z), E, F, fl, g,
+                   {"K1": K1})
+
+
+def thacker_bowl(N=4, K1=128, g=9.81, h0=0.25, a=1.0, sigma=0.5, rotate_seed=None) -> Problem:
+    """Oscillating lake in the parabolic bowl b = h0 (x^2+y^2)/a^2 on [-2,2]^2
+    (curved map x += 0.05 sin(pi x/2) sin(pi y/2), same for y), initial state
+    of the analytic solution at t = 0: wet disc (x-sigma)^2 + y^2 < a^2."""
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, K1, K1, (-2.0, 2.0, -2.0, 2.0),
+                                           _sine_map(0.05, math.pi / 2), rotate_seed)
+    b = h0 * (xw ** 2 + yw ** 2) / a ** 2
+    W = thacker_state(xw, yw, b, 0.0, g, h0, a, sigma)
+    p = Problem("thacker_bowl", N, K1, K1, x, y, b, W, E, F, fl, g,
+                {"h0": h0, "a": a, "sigma": sigma, "omega": math.sqrt(2 * g * h0) / a})
+    p.meta["xw"], p.meta["yw"] = xw, yw
+    return p
+
+
+def thacker_state(xw, yw, b, t, g=9.81, h0=0.25, a=1.0, sigma=0.5):
+    """Analytic oscillating-lake solution at time t (Sec. 6.2)."""
+    om = math.sqrt(2 * g * h0) / a
+    h = np.maximum(0.0, sigma * h0 / a ** 2 * (2 * xw * math.cos(om * t) + 2 * yw * math.sin(om * t) - sigma)
+                   + h0 - b)
+    u = np.where(h > 0, -sigma * om * math.sin(om * t), 0.0)
+    v = np.where(h > 0, sigma * om * math.cos(om * t), 0.0)
+    return _state(h, u, v)
+
+
+def random_smooth(N=3, K1=4, seed=0, rotate_seed=None, g=9.81, dh=0.2, du=0.5,
+                  flat=False, Kx=None, Ky=None) -> Problem:
+    """Smooth random periodic state (h in [1-dh, 1+dh], |u|,|v| <= du) on the
+    curved [0,2]^2 mesh with a smooth random bathymetry (flat if asked)."""
+    Kx = Kx or K1
+    Ky = Ky or K1
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, Kx, Ky, (0.0, 2.0, 0.0, 2.0),
+                                           _sine_map(0.05, math.pi), rotate_seed)
+    rng = np.random.default_rng(seed)
+    b = np.zeros_like(xw) if flat else 0.1 * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+    h = 1.0 + dh * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+    u = du * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+    v = du * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+    return Problem("random_smooth", N, Kx, Ky, x, y, b, _state(h, u, v), E, F, fl, g)
+
+
+def random_rough(N=3, K1=4, seed=0, rotate_seed=None, g=9.81, dry_fraction=0.0) -> Problem:
+    """Non-smooth random nodal state (independent noise per node) on a smooth
+    bathymetry; with dry_fraction > 0 that share of nodes is set dry."""
+    p = random_smooth(N, K1, seed, rotate_seed, g)
+    rng = np.random.default_rng(seed + 1000)
+    h = 1.0 + 0.3 * rng.uniform(-1, 1, size=p.b.shape)
+    u = 0.5 * rng.uniform(-1, 1, size=p.b.shape)
+    v = 0.5 * rng.uniform(-1, 1, size=p.b.shape)
+    if dry_fraction > 0:
+        dry = rng.uniform(size=p.b.shape) < dry_fraction
+        h = np.where(dry, 0.0, h)
+        u = np.where(dry, 0.0, u)
+        v = np.where(dry, 0.0, v)
+    p.W = _state(h, u, v)
+    p.name = "random_rough"
+    return p
+
+
+CONFIGS = {
+    "lake_hump": lake_hump,
+    "dam_break": dam_break,
+    "thacker_bowl": thacker_bowl,
+    "random_smooth": random_smooth,
+    "random_rough": random_rough,
+    "lake_at_rest_kinked": lake_at_rest_kinked,
+}

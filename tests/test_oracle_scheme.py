@@ -1,0 +1,349 @@
+"""Pins of the oracle's semi-discrete operator, limiter and time stepping
+against what the paper and the mathematics fix:
+
+  free stream and lake at rest (Lemma ESDGSEM, well-balance) on curved,
+  rotated-element meshes; mass conservation; the entropy identities of the
+  EC scheme, of the ES dissipation and of the artificial viscosity (Thm. 1);
+  consistency with the PDE (Eq. sw-invisc, Eq. sw-visc) at the expected order
+  on a manufactured smooth state; the modal indicator (App. A) on known
+  Legendre data; the limiter (Eq. PosPres, Lemma ESPP); positivity of the
+  means under the Lemma PosPres time step; RK time-convergence order.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import refmath
+from oracle import oracle as O
+from paper_1804_02221_gb300 import inputs as I
+
+
+def weighted(prob, a):
+    """sum_k sum_ij J w_i w_j a_ij (a: [..., K, n, n])."""
+    geo = refmath.geometry(prob.x, prob.y, prob.N)
+    ww = refmath.quad_weights(prob.N)
+    return np.sum(a * geo[4] * ww, axis=(-3, -2, -1))
+
+
+def term_scale(prob):
+    """Magnitude of the flux-divergence terms: g h^2 / (J / Jsurf)."""
+    geo = refmath.geometry(prob.x, prob.y, prob.N)
+    h = np.abs(prob.W[0]).max()
+    return prob.g * h * h * prob.N ** 2 / np.sqrt(geo[4].min())
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 5, 8])
+def test_free_stream(N):
+    p = I.random_smooth(N=N, K1=3, seed=3, rotate_seed=11, flat=True)
+    p.W = np.stack([np.ones_like(p.b), 0.3 * np.ones_like(p.b), -0.2 * np.ones_like(p.b)])
+    R = O.Oracle(p, flux=1, av=True, eps0=0.02).rhs(p.W)
+    assert np.abs(R).max() < 1e-13 * term_scale(p)
+
+
+@pytest.mark.parametrize("N,rot", [(1, None), (3, 7), (4, 8), (7, 9)])
+def test_lake_at_rest(N, rot):
+    p = I.lake_at_rest_kinked(N=N, K1=5, rotate_seed=rot)
+    o = O.Oracle(p, flux=1, av=True, eps0=0.05, sigma_min=-9.0, sigma_max=-8.0, limiter=True)
+    R = o.rhs(p.W)
+    assert o.epsilon().max() > 0  # the kinked bathymetry switches the viscosity on
+    assert np.abs(R).max() < 1e-13 * term_scale(p)
+    W, rc, dt = o.step(p.W, 0.0, 20)
+    assert rc == 0
+    assert np.abs(W[0] + p.b - 1.0).max() < 1e-12
+    assert np.abs(W[1:]).max() < 1e-12
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+@pytest.mark.parametrize("N", [2, 3, 6])
+def test_mass_conservation(flux, N):
+    p = I.random_rough(N=N, K1=3, seed=N, rotate_seed=N)
+    R = O.Oracle(p, flux=flux, av=True, eps0=0.05).rhs(p.W)
+    tot = weighted(p, np.abs(R[0]))
+    assert abs(weighted(p, R[0])) < 1e-14 * tot
+
+
+@pytest.mark.parametrize("N,rot", [(1, None), (3, 5), (4, None), (7, 6)])
+def test_entropy_conservation_ec(N, rot):
+    """EC surface flux, no viscosity: sum J w w q.R vanishes (Lemma ESDGSEM)."""
+    p = I.random_rough(N=N, K1=3, seed=10 + N, rotate_seed=rot)
+    R = O.Oracle(p, flux=0).rhs(p.W)
+    q = refmath.entropy_vars(p.W, p.b, p.g)
+    terms = weighted(p, q * R)
+    assert abs(terms.sum()) < 1e-13 * weighted(p, np.abs(q * R)).sum()
+
+
+def es_dissipation_sum(p):
+    """-1/2 sum_faces sum_p w_p Jsurf [[q~]]^T R~|L~|R~^T [[q~]] from the face states."""
+    N, g = p.N, p.g
+    geo = refmath.geometry(p.x, p.y, N)
+    _, w = refmath.lgl(N)
+    h, u, v = refmath.primitives(p.W)
+    tot = 0.0
+    for (k, f, kk, ff, fl) in refmath.unique_faces(p):
+        nx, ny = (a[k] for a in refmath.outward_normal(geo, f))
+        js = np.hypot(nx, ny)
+        nx, ny = nx / js, ny / js
+        sl = lambda a, face, e: refmath.face_slice(a, face)[e]
+        hm, um, vm, bm = sl(h, f, k), sl(u, f, k), sl(v, f, k), sl(p.b, f, k)
+        hp, up, vp, bp = sl(h, ff, kk), sl(u, ff, kk), sl(v, ff, kk), sl(p.b, ff, kk)
+        if fl:
+            hp, up, vp, bp = hp[::-1], up[::-1], vp[::-1], bp[::-1]
+        utm, vtm = nx * um + ny * vm, -ny * um + nx * vm
+        utp, vtp = nx * up + ny * vp, -ny * up + nx * vp
+        dq = np.stack([g * (hp + bp) - 0.5 * (utp ** 2 + vtp ** 2) - g * (hm + bm) + 0.5 * (utm ** 2 + vtm ** 2),
+                       utp - utm, vtp - vtm])
+        ha, ua, va = 0.5 * (hm + hp), 0.5 * (utm + utp), 0.5 * (vtm + vtp)
+        ca = 0.5 * (np.sqrt(g * hm) + np.sqrt(g * hp))
+        one, zero = np.ones_like(ha), np.zeros_like(ha)
+        R = np.array([[one, zero, one], [ua + ca, zero, ua - ca], [va, one, va]])  # [3,3,n]
+        lam = np.stack([np.abs(ua + ca) / (2 * g), np.abs(ha * ua), np.abs(ua - ca) / (2 * g)])
+        RTdq = np.einsum("ban,bn->an", R, dq)
+        tot += -0.5 * np.sum(w * js * np.sum(lam * RTdq ** 2, axis=0))
+    return tot
+
+
+@pytest.mark.parametrize("N,rot", [(2, None), (3, 4), (5, 5)])
+def test_es_dissipation_identity(N, rot):
+    p = I.random_rough(N=N, K1=3, seed=20 + N, rotate_seed=rot)
+    Res = O.Oracle(p, flux=1).rhs(p.W)
+    Rec = O.Oracle(p, flux=0).rhs(p.W)
+    q = refmath.entropy_vars(p.W, p.b, p.g)
+    lhs = weighted(p, q * (Res - Rec)).sum()
+    rhs = es_dissipation_sum(p)
+    assert rhs < 0
+    assert abs(lhs - rhs) < 1e-12 * weighted(p, np.abs(q * Res)).sum()
+
+
+@pytest.mark.parametrize("N,rot", [(1, None), (3, 3), (4, None), (6, 2)])
+def test_av_entropy_identity(N, rot):
+    """Thm. 1: sum J w w q.(R_AV - R) = -sum_k eps_k sum J w w h (U1^2+U2^2+V1^2+V2^2)."""
+    p = I.random_rough(N=N, K1=3, seed=30 + N, rotate_seed=rot)
+    o = O.Oracle(p, flux=1, av=True, eps0=0.03, sigma_min=-6.0, sigma_max=-0.5)
+    Rav = o.rhs(p.W)
+    eps, grads = o.av_fields(p.W)
+    assert eps.max() > 0 and np.any(eps < 0.03)
+    R = O.Oracle(p, flux=1).rhs(p.W)
+    q = refmath.entropy_vars(p.W, p.b, p.g)
+    lhs = weighted(p, q * (Rav - R)).sum()
+    rhs = -weighted(p, eps[:, None, None] * p.W[0] * np.sum(grads ** 2, axis=0))
+    assert rhs < 0
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs) + 1e-14 * weighted(p, np.abs(q * R)).sum()
+
+
+# ---------------------------------------------------------------------------
+# Consistency with the PDE on a manufactured smooth state
+# ---------------------------------------------------------------------------
+
+def _manufactured(N, K1, eps0=None):
+    sp = pytest.importorskip("sympy")
+    x, y, xw, yw, E, F, fl = I.periodic_mesh(N, K1, K1, (0.0, 2.0, 0.0, 2.0),
+                                             lambda X, Y: (0.05 * np.sin(np.pi * X) * np.sin(np.pi * Y),) * 2,
+                                             rotate_seed=K1)
+    X, Y = sp.symbols("x y")
+    g = 9.81
+    hs = 1 + 0.1 * sp.sin(sp.pi * X) * sp.cos(sp.pi * Y)
+    us = 0.3 * sp.sin(sp.pi * (X + Y))
+    vs = 0.2 * sp.cos(sp.pi * X)
+    bs = 0.1 * sp.sin(sp.pi * X) * sp.sin(sp.pi * Y)
+    f = [hs * us, hs * us ** 2 + g * hs ** 2 / 2, hs * us * vs]
+    gg = [hs * vs, hs * us * vs, hs * vs ** 2 + g * hs ** 2 / 2]
+    src = [0, -g * hs * sp.diff(bs, X), -g * hs * sp.diff(bs, Y)]
+    wt = [-sp.diff(f[c], X) - sp.diff(gg[c], Y) + src[c] for c in range(3)]
+    visc = [0, sp.diff(hs * sp.diff(us, X), X) + sp.diff(hs * sp.diff(us, Y), Y),
+            sp.diff(hs * sp.diff(vs, X), X) + sp.diff(hs * sp.diff(vs, Y), Y)]
+    lam = lambda e: sp.lambdify((X, Y), e, "numpy")
+    h, u, v, b = (lam(e)(xw, yw) * np.ones_like(xw) for e in (hs, us, vs, bs))
+    W = np.stack([h, h * u, h * v])
+    Wt = np.stack([lam(e)(xw, yw) * np.ones_like(xw) for e in wt])
+    Vt = np.stack([lam(e)(xw, yw) * np.ones_like(xw) for e in visc])
+    p = I.Problem("manufactured", N, K1, K1, x, y, b, W, E, F, fl, g)
+    return p, Wt, Vt
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_consistency_order(N):
+    errs = []
+    Ks = (4, 8, 16)
+    for K1 in Ks:
+        p, Wt, _ = _manufactured(N, K1)
+        R = O.Oracle(p, flux=1).rhs(p.W)
+        errs.append(np.abs(R - Wt).max())
+    rate = math.log(errs[-2] / errs[-1], 2)
+    assert rate > N - 0.5, (errs, rate)
+
+
+@pytest.mark.parametrize("N", [3, 4])
+def test_viscous_consistency_order(N):
+    """With eps = eps0 in every element the viscous part converges to
+    eps0 div(h grad u), eps0 div(h grad v) (Eq. sw-visc)."""
+    eps0 = 0.01
+    errs = []
+    for K1 in (4, 8, 16):
+        p, _, Vt = _manufactured(N, K1)
+        Rav = O.Oracle(p, flux=1, av=True, eps0=eps0, sigma_min=-301.0, sigma_max=-300.0).rhs(p.W)
+        R = O.Oracle(p, flux=1).rhs(p.W)
+        errs.append(np.abs((Rav - R) - eps0 * Vt).max() / eps0)
+    rate = math.log(errs[-2] / errs[-1], 2)
+    assert rate > N - 1.5, (errs, rate)
+
+
+# ---------------------------------------------------------------------------
+# Indicator (App. A)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N", [2, 3, 5, 7])
+def test_indicator_closed_form(N):
+    """h = c + Ltilde_N(xi) has modal coefficients Qhat_00 = 2c and
+    Qhat_N0 = sqrt(2), so sigma = log10(2 / (4 c^2 + 2))."""
+    from numpy.polynomial import legendre as npleg
+    p = I.random_smooth(N=N, K1=2, seed=1)
+    xi, _ = refmath.lgl(N)
+    LN = npleg.legval(xi, [0] * N + [1]) * math.sqrt(N + 0.5)
+    cs = np.array([1.0, 2.0, 5.0, 20.0])
+    h = cs[:, None, None] + LN[None, None, :] * np.ones((1, N + 1, 1))
+    p.W = np.stack([h, 0 * h, 0 * h])
+    sigma = np.log10(2.0 / (4 * cs ** 2 + 2))
+    smin, smax, eps0 = -4.0, -0.2, 0.7
+    o = O.Oracle(p, flux=1, av=True, eps0=eps0, sigma_min=smin, sigma_max=smax)
+    eps, _ = o.av_fields(p.W)
+    ref = np.where(sigma <= smin, 0.0, np.where(sigma >= smax, eps0,
+                   0.5 * eps0 * (1 + np.sin(np.pi * (sigma - 0.5 * (smax + smin)) / (smax - smin)))))
+    assert np.allclose(eps, ref, rtol=1e-12, atol=1e-15)
+    # a pure degree-(N-1) mode in either direction: Qhat_00 = 2c,
+    # Qhat_{N-1,0} (or Qhat_{0,N-1}) = sqrt(2); ratio1 = 0 and
+    # ratio2 = 2 / (4c^2 + 2); the eta-direction top mode feeds ratio1 likewise
+    LN1 = npleg.legval(xi, [0] * (N - 1) + [1]) * math.sqrt(N - 0.5)
+    for prof, axis in ((LN1, "xi"), (LN1, "eta"), (LN, "eta")):
+        if axis == "xi":
+            h = cs[:, None, None] + prof[None, None, :] * np.ones((1, N + 1, 1))
+        else:
+            h = cs[:, None, None] + prof[None, :, None] * np.ones((1, 1, N + 1))
+        p.W = np.stack([h, 0 * h, 0 * h])
+        eps, _ = O.Oracle(p, flux=1, av=True, eps0=eps0, sigma_min=smin, sigma_max=smax).av_fields(p.W)
+        assert np.allclose(eps, ref, rtol=1e-12, atol=1e-15), (axis, eps, ref)
+    # a polynomial of degree <= N-2 in each direction has no energy in the
+    # modes of degree N or N-1 that the two ratios of Eq. sigmadof measure
+    h2 = 1.0 + 0.3 * xi[None, :] ** (N - 2) * xi[:, None] ** (N - 2)
+    p.W = np.stack([np.broadcast_to(h2, p.b.shape).copy(), 0 * p.b, 0 * p.b])
+    eps, _ = O.Oracle(p, flux=1, av=True, eps0=eps0, sigma_min=smin, sigma_max=smax).av_fields(p.W)
+    assert np.all(eps == 0.0)
+
+
+# ---------------------------------------------------------------------------
+# Limiter (Eq. PosPres, Lemma ESPP) and positivity (Lemma PosPres)
+# ---------------------------------------------------------------------------
+
+def element_means(p, W):
+    geo = refmath.geometry(p.x, p.y, p.N)
+    ww = refmath.quad_weights(p.N) * geo[4]
+    return np.sum(W * ww, axis=(-2, -1)) / np.sum(ww, axis=(-2, -1))
+
+
+def element_entropy(p, W):
+    h, u, v = refmath.primitives(W)
+    e = 0.5 * h * (u * u + v * v) + 0.5 * p.g * h * h + p.g * h * p.b
+    geo = refmath.geometry(p.x, p.y, p.N)
+    return np.sum(e * refmath.quad_weights(p.N) * geo[4], axis=(-2, -1))
+
+
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_limiter(N):
+    p = I.random_rough(N=N, K1=4, seed=40 + N, rotate_seed=N)
+    rng = np.random.default_rng(N)
+    h = 0.1 + 0.3 * rng.uniform(-1, 1, size=p.b.shape)
+    W = np.stack([h, h * rng.uniform(-1, 1, size=h.shape), h * rng.uniform(-1, 1, size=h.shape)])
+    W[:, ::3] = np.abs(W[:, ::3])  # some untouched elements
+    # keep every element mean of h positive (the limiter's precondition)
+    W[0] += np.maximum(0.0, 0.05 - element_means(p, W)[0])[:, None, None]
+    o = O.Oracle(p, flux=1, limiter=True, h_tol=1e-4)
+    Wl, rc = o.limit(W)
+    assert rc == 0
+    m0, m1 = element_means(p, W), element_means(p, Wl)
+    assert np.allclose(m0[0], m1[0], rtol=1e-13, atol=1e-15)
+    assert Wl[0].min() > -1e-15
+    # Lemma ESPP's Jensen argument needs the entropy convex along the segment
+    # from each node to the mean; at the nodes with h < 0 that trigger the
+    # limiter it is not defined, so only Jensen's lower bound on the limited
+    # (admissible) state is checked here: element entropy >= |E| e(mean).
+    geo = refmath.geometry(p.x, p.y, p.N)
+    vol = np.sum(refmath.quad_weights(p.N) * geo[4], axis=(-2, -1))
+    mb = element_means(p, p.b[None])[0]
+    hm, mu, mv = element_means(p, Wl)
+    e_mean = 0.5 * (mu * mu + mv * mv) / hm + 0.5 * p.g * hm * hm + p.g * hm * mb
+    lin = element_means(p, (p.g * Wl[0] * p.b)[None])[0] - p.g * hm * mb  # b varies in the element
+    assert np.all(element_entropy(p, Wl) >= vol * (e_mean + lin) - 1e-12)
+    # elements with a non-negative minimum are not touched, except the h_tol cut
+    ok = W[0].min(axis=(-2, -1)) >= 0
+    same = np.where(W[0] >= 1e-4, W, np.stack([W[0], 0 * W[0], 0 * W[0]]))
+    assert np.array_equal(Wl[:, ok], same[:, ok])
+    # nodes below h_tol carry no momentum
+    assert np.all(Wl[1:][:, Wl[0] < 1e-4] == 0)
+
+
+def test_limiter_negative_mean_reports_error():
+    p = I.random_smooth(N=3, K1=2, seed=2)
+    W = p.W.copy()
+    W[0, 1] = -0.5
+    _, rc = O.Oracle(p, limiter=True).limit(W)
+    assert rc == O.ERR_NEG_MEAN
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_positivity_of_means_under_dt_pos(N):
+    """Lemma PosPres: from nodal h >= 0, one Euler step with dt <= dt_pos keeps
+    every element mean non-negative (ES flux, with artificial viscosity)."""
+    for seed in range(4):
+        p = I.random_rough(N=N, K1=4, seed=50 + seed, rotate_seed=seed, dry_fraction=0.4)
+        o = O.Oracle(p, flux=1, av=True, eps0=0.05, limiter=True)
+        W0, rc = o.limit(p.W)
+        assert rc == 0
+        _, dt_pos = o.max_dt(W0)
+        assert math.isfinite(dt_pos) and dt_pos > 0
+        R = o.rhs(W0)
+        means = element_means(p, W0 + dt_pos * R)[0]
+        assert means.min() > -1e-14 * max(1.0, W0[0].max())
+
+
+def test_thacker_positivity_and_mass():
+    """Wet/dry oscillating lake, SSPRK3 with dt = min(CFL, positivity): every
+    stage keeps non-negative means, and mass is conserved."""
+    p = I.thacker_bowl(N=3, K1=12)
+    o = O.Oracle(p, flux=1, av=True, eps0=0.01, limiter=True, rk=1, cfl=0.3)
+    W, rc = o.limit(p.W)
+    m0 = o.mass(W)[0]
+    W, rc, dt = o.step(W, 0.0, 30)
+    assert rc == 0
+    assert W[0].min() > -1e-14
+    assert abs(o.mass(W)[0] - m0) < 1e-13 * m0
+
+
+def test_lsrk_order_conditions():
+    """The 2N-storage coefficients, turned into a Butcher tableau, satisfy
+    the eight classical conditions of order 4 (to round-off)."""
+    A, B = O.lsrk_coefficients()
+    S = 5
+    a = np.zeros((S + 1, S))
+    for s in range(1, S + 1):
+        for j in range(s):
+            a[s, j] = sum(B[i] * np.prod(A[j + 1:i + 1]) for i in range(j, s))
+    b, c, a = a[S], a[:S].sum(axis=1), a[:S]
+    conds = [(b.sum(), 1), (b @ c, 1 / 2), (b @ c ** 2, 1 / 3), (b @ a @ c, 1 / 6),
+             (b @ c ** 3, 1 / 4), ((b * c) @ a @ c, 1 / 8), (b @ a @ c ** 2, 1 / 12),
+             (b @ a @ a @ c, 1 / 24)]
+    for val, target in conds:
+        assert abs(val - target) < 1e-14
+
+
+@pytest.mark.parametrize("rk,order", [(0, 4), (1, 3)])
+def test_time_order(rk, order):
+    p = I.lake_hump(N=3, K1=4, amp=0.05)
+    o = O.Oracle(p, flux=1, rk=rk)
+    T = 0.04
+    ref, _, _ = o.step(p.W, T / 256, 256)
+    errs = []
+    for ns in (4, 8, 16):
+        W, _, _ = o.step(p.W, T / ns, ns)
+        errs.append(np.abs(W - ref).max())
+    rate = math.log(errs[-2] / errs[-1], 2)
+    assert rate > order - 0.3, (errs, rate)
