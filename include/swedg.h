@@ -1,0 +1,156 @@
+/*
+ * swedg: GB300-native right-hand side and time stepping of the entropy-stable
+ * nodal DGSEM for the 2D shallow water equations on curvilinear quadrilateral
+ * meshes with wet/dry fronts (Wintermeyer, Winters, Gassner, Warburton 2018).
+ *
+ * C ABI: plain pointers and sizes. All floating point is IEEE binary64.
+ *
+ * Nodal layout (every nodal array, host or device): [K][n][n], n = N+1,
+ * index (k*n + j)*n + i, i the xi index (fastest), j the eta index. A state
+ * W or a right-hand side R is three such planes (h, hu, hv) back to back:
+ * W[c*K*n*n + (k*n + j)*n + i].
+ *
+ * Element faces: 0: eta=-1 (j=0), 1: xi=+1 (i=N), 2: eta=+1 (j=N),
+ * 3: xi=-1 (i=0). Face node p runs along increasing xi (faces 0, 2) or eta
+ * (faces 1, 3). Node p of face (k,f) meets node (flip ? N-p : p) of face
+ * (EToE[k*4+f], EToF[k*4+f]). Every face must have a neighbour (periodic or
+ * otherwise closed meshes); the connectivity must be reciprocal.
+ *
+ * Ownership: the caller owns W, R and every pointer it passes; a context owns
+ * the geometry and the scratch buffers it allocates on the device at
+ * swe_create and releases at swe_destroy. Device pointers must stay valid
+ * while work queued on the given stream runs. A NULL stream is the legacy
+ * default stream.
+ *
+ * Errors: every int-returning call returns SWE_OK (0) or a negative code; the
+ * text of the last error of the calling thread is swe_last_error(). No call
+ * traps or waits without bound on the device.
+ */
+#ifndef SWEDG_H
+#define SWEDG_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SWE_OK 0
+#define SWE_ERR_ARG (-1)       /* invalid argument or unsupported input */
+#define SWE_ERR_GEOM (-2)      /* non-positive Jacobian at a node */
+#define SWE_ERR_NEG_MEAN (-3)  /* an element mean water height became negative */
+#define SWE_ERR_NONFINITE (-4) /* a non-finite value appeared in the state */
+#define SWE_ERR_CUDA (-5)      /* a CUDA runtime call failed */
+
+#define SWE_NMAX 12
+
+typedef struct swe_ctx swe_ctx;
+
+/* Scheme parameters.
+ * flux:      0 entropy-conservative interface flux (Eq. surfaceFluxes),
+ *            1 entropy-stable flux (Eq. fesandges, rotated as in App. B).
+ * av:        1 adds the BR1 artificial viscosity of Sec. 3 (Thm. 1) with the
+ *            element viscosity of App. A.
+ * eps0:      base viscosity epsilon_0 of App. A.
+ * sigma_min, sigma_max: ramp of App. A; NaN selects -4 log10(N) -/+ 1 (the
+ *            paper gives no values).
+ * limiter:   1 applies the positivity limiter (Eq. PosPres) and the h_tol
+ *            momentum cut after every Runge-Kutta stage.
+ * h_tol:     water height below which the momentum is set to zero (Sec. 6.1,
+ *            1e-4); NaN selects 1e-4.
+ * rk:        0 five-stage fourth-order 2N-storage Runge-Kutta (Carpenter &
+ *            Kennedy), 1 SSPRK3 (Eq. RKSSP).
+ * cfl:       CFL number of the time-step rule
+ *            dt = cfl * 2/(N+1) * min_nodes J / (lambda_xi + lambda_eta). */
+typedef struct {
+    int flux;
+    int av;
+    double eps0;
+    double sigma_min;
+    double sigma_max;
+    int limiter;
+    double h_tol;
+    int rk;
+    double cfl;
+} swe_params;
+
+/* Build a context (Sec. 2.1: curvilinear map, metric terms, Jacobian
+ * Eq. JacobianDef, surface Jacobian Eq. SurfJac; Eq. SourceDisc's split-form
+ * bathymetry derivatives). Host inputs, copied:
+ *   x, y, b  [K][n][n] node coordinates and bathymetry (b must agree on the
+ *            two sides of every face node);
+ *   EToE, EToF, flip [K][4] connectivity as described above;
+ *   g > 0 gravity; p parameters (copied).
+ * Uses the current CUDA device. 1 <= N <= SWE_NMAX, K >= 1.
+ * Returns SWE_ERR_GEOM if J <= 0 at a node, SWE_ERR_ARG for bad
+ * connectivity, sizes or parameters, SWE_ERR_CUDA on allocation failure. */
+int swe_create(int N, int K, const double* x, const double* y, const int32_t* EToE,
+               const int32_t* EToF, const int32_t* flip, const double* b, double g,
+               const swe_params* p, swe_ctx** out);
+
+/* Release a context (waits for its work on the device to finish). */
+void swe_destroy(swe_ctx* ctx);
+
+/* Semi-discrete operator R = W_t of Eq. CurvilinearECDGSEMviscous divided by
+ * J (Eq. Curvilinear ECDGSEM without viscosity when av = 0): volume term by
+ * flux differencing (Eq. fluxDiffFormF, Eq. Fmij, Eq. volumeFluxes),
+ * interface flux, source, BR1 viscous terms (Eq. BR1, Eq. ViscTermsDisc).
+ * W, R: device pointers, 3*K*n*n doubles each, not overlapping. Asynchronous
+ * on `stream` (a cudaStream_t). */
+int swe_rhs(swe_ctx* ctx, const double* W, double* R, void* stream);
+
+/* Positivity limiter (Eq. PosPres) and the h_tol momentum cut on device
+ * state W in place. Asynchronous; an element with a negative mean is left as
+ * is and recorded in the status read by swe_status. */
+int swe_limit(swe_ctx* ctx, double* W, void* stream);
+
+/* Largest admissible time step for device state W: the CFL rule (dt_cfl) and
+ * the positivity restrictions of Lemma PosPres, Eq. CFLConstraints (dt_pos,
+ * +inf when limiter = 0 or flux = 0). Host outputs; synchronises `stream`. */
+int swe_max_dt(swe_ctx* ctx, const double* W, double* dt_cfl, double* dt_pos, void* stream);
+
+/* Advance device state W in place by nsteps steps of the chosen Runge-Kutta
+ * scheme (with the limiter after every stage when enabled). dt > 0 is a fixed
+ * step; dt <= 0 recomputes min(dt_cfl, dt_pos) at the start of every step on
+ * the device. Synchronises `stream` at the end and checks the device status:
+ * if an element mean became negative or a value became non-finite, W is
+ * restored to the state at the start of the failing step, and
+ * SWE_ERR_NEG_MEAN or SWE_ERR_NONFINITE is returned (the caller may retry
+ * with a smaller dt). dt_last (host, nullable) receives the last step size. */
+int swe_step(swe_ctx* ctx, double* W, double dt, int nsteps, double* dt_last, void* stream);
+
+/* Discrete integrals of device state W: out3 = sum_k sum_ij J w_i w_j W
+ * (mass and momenta), E = sum J w_i w_j e(W) with e of Eq. entropyFunction.
+ * Host outputs; synchronise `stream`; deterministic summation order. */
+int swe_mass(swe_ctx* ctx, const double* W, double* out3, void* stream);
+int swe_entropy(swe_ctx* ctx, const double* W, double* E, void* stream);
+
+/* Copy the element viscosities epsilon_k (App. A) of the last swe_rhs into
+ * device array eps[K]. Asynchronous. */
+int swe_get_epsilon(swe_ctx* ctx, double* eps, void* stream);
+
+/* Device status bits accumulated since the last call (1: negative element
+ * mean, 2: non-finite value), then cleared. Synchronises `stream`. */
+int swe_status(swe_ctx* ctx, int* bits, void* stream);
+
+/* Kernel timing of the library's own launches. After swe_timing(ctx, 1),
+ * every kernel launch is bracketed by CUDA events on its stream;
+ * swe_timing_read returns, for kernel class `which` (0 volume, 1 interface
+ * flux, 2 primitives, 3 AV indicator/gradient, 4 viscous interface, 5 stage
+ * update/limiter, 6 time step, 7 reductions), the summed event time in
+ * milliseconds and the launch count since swe_timing(ctx, 1) (synchronises).
+ * swe_launches returns the number of kernels the context launched so far. */
+int swe_timing(swe_ctx* ctx, int on);
+int swe_timing_read(swe_ctx* ctx, int which, double* ms, int64_t* launches);
+int64_t swe_launches(const swe_ctx* ctx);
+
+/* Sizes of a context: N, K and the number of unique faces. */
+int swe_info(const swe_ctx* ctx, int* N, int* K, int* nfaces);
+
+/* Text of the last error on the calling thread ("" if none). */
+const char* swe_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,509 @@
+// C ABI of the swedg library: context construction (host geometry, face
+// lists, device upload), the right-hand-side and time-step orchestration,
+// diagnostics and timing.
+#include <math.h>
+#include <string.h>
+
+#include <mutex>
+#include <set>
+#include <string>
+#include <vector>
+
+#include "swe_internal.h"
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const std::string& msg) {
+    g_last_error = msg;
+    return code;
+}
+
+int cuda_fail(cudaError_t e, const char* where) {
+    return fail(SWE_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+// Carpenter & Kennedy (1994), five-stage fourth-order 2N-storage scheme.
+const double kLsrkA[5] = {0.0, -567301805773.0 / 1357537059087.0, -2404267990393.0 / 2016746695238.0,
+                          -3550918686646.0 / 2091501179385.0, -1275806237668.0 / 842570457699.0};
+const double kLsrkB[5] = {1432997174477.0 / 9575080441755.0, 5161836677717.0 / 13612068292357.0,
+                          1720146321549.0 / 2090206949498.0, 3134564353537.0 / 4481467310338.0,
+                          2277821191437.0 / 14882151754819.0};
+
+constexpr int kEventPairs = 8192;
+
+void init_device_tables(int device) {
+    static std::mutex mu;
+    static std::set<int> done;
+    std::lock_guard<std::mutex> lock(mu);
+    if (done.count(device)) return;
+    swe::init_tables_volume();
+    swe::init_tables_face();
+    swe::init_tables_av();
+    done.insert(device);
+}
+
+// Volume node (i, j) of face node p on face f.
+inline void face_node(int N, int f, int p, int& i, int& j) {
+    switch (f) {
+        case 0: i = p; j = 0; break;
+        case 1: i = N; j = p; break;
+        case 2: i = p; j = N; break;
+        default: i = 0; j = p; break;
+    }
+}
+
+template <typename T>
+T* dev_upload(swe_ctx* c, const std::vector<T>& h, cudaError_t& err) {
+    void* p = nullptr;
+    size_t bytes = h.size() * sizeof(T);
+    if (bytes == 0) bytes = sizeof(T);
+    err = cudaMalloc(&p, bytes);
+    if (err != cudaSuccess) return nullptr;
+    c->allocations.push_back(p);
+    if (!h.empty()) err = cudaMemcpy(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice);
+    return static_cast<T*>(p);
+}
+
+double* dev_alloc(swe_ctx* c, size_t count, cudaError_t& err) {
+    void* p = nullptr;
+    err = cudaMalloc(&p, (count ? count : 1) * sizeof(double));
+    if (err != cudaSuccess) return nullptr;
+    c->allocations.push_back(p);
+    return static_cast<double*>(p);
+}
+
+void free_all(swe_ctx* c) {
+    for (void* p : c->allocations) cudaFree(p);
+    c->allocations.clear();
+    for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
+    c->ev.clear();
+}
+
+}  // namespace
+
+namespace swe {
+
+Timed::Timed(swe_ctx* c_, int cls, cudaStream_t s_) : c(c_), s(s_) {
+    c->launches++;
+    if (c->timing && c->ev_used < (int)c->ev_class.size()) {
+        idx = c->ev_used++;
+        c->ev_class[idx] = cls;
+        cudaEventRecord(c->ev[2 * idx], s);
+    }
+}
+
+Timed::~Timed() {
+    if (idx >= 0) cudaEventRecord(c->ev[2 * idx + 1], s);
+}
+
+}  // namespace swe
+
+// ---------------------------------------------------------------------------
+// Context
+// ---------------------------------------------------------------------------
+
+extern "C" int swe_create(int N, int K, const double* x, const double* y, const int32_t* EToE,
+                          const int32_t* EToF, const int32_t* flip, const double* b, double g,
+                          const swe_params* p, swe_ctx** out) {
+    using namespace swe;
+    if (!out) return fail(SWE_ERR_ARG, "swe_create: out is NULL");
+    *out = nullptr;
+    if (!x || !y || !EToE || !EToF || !flip || !b || !p)
+        return fail(SWE_ERR_ARG, "swe_create: NULL input");
+    if (N < 1 || N > NMAX) return fail(SWE_ERR_ARG, "swe_create: N must be in 1..12");
+    if (K < 1) return fail(SWE_ERR_ARG, "swe_create: K must be >= 1");
+    if (!(g > 0.0) || !isfinite(g)) return fail(SWE_ERR_ARG, "swe_create: g must be positive");
+    if (p->flux != 0 && p->flux != 1) return fail(SWE_ERR_ARG, "swe_create: flux must be 0 or 1");
+    if (p->rk != 0 && p->rk != 1) return fail(SWE_ERR_ARG, "swe_create: rk must be 0 or 1");
+    if (p->av && !(p->eps0 >= 0.0)) return fail(SWE_ERR_ARG, "swe_create: eps0 must be >= 0");
+    const int n = N + 1, nn = n * n;
+    const long long KN = (long long)K * nn, KS = (long long)K * 4 * n;
+    if (KN * 3 > 2147483647LL) return fail(SWE_ERR_ARG, "swe_create: mesh too large for 32-bit node ids");
+    // connectivity
+    for (int k = 0; k < K; ++k)
+        for (int f = 0; f < 4; ++f) {
+            const int kk = EToE[4 * k + f], ff = EToF[4 * k + f];
+            if (kk < 0 || kk >= K || ff < 0 || ff > 3)
+                return fail(SWE_ERR_ARG, "swe_create: face without neighbour (boundary faces are not supported) at element " +
+                                             std::to_string(k));
+            if ((kk == k && ff == f) || EToE[4 * kk + ff] != k || EToF[4 * kk + ff] != f ||
+                flip[4 * kk + ff] != flip[4 * k + f] || (flip[4 * k + f] != 0 && flip[4 * k + f] != 1))
+                return fail(SWE_ERR_ARG, "swe_create: connectivity not reciprocal at element " + std::to_string(k));
+        }
+    const Tables& T = tables();
+    const double* D = T.D + mat_offset(N);
+    const double* w = T.w + vec_offset(N);
+
+    // ---- host geometry (Sec. 2.1) ----
+    std::vector<double> axx(KN), axy(KN), aex(KN), aey(KN), rJ(KN), wJ(KN), srcx(KN), srcy(KN), bn(KN),
+        cfln(KN), rvol(K), Jv(KN);
+    std::vector<double> tmp(4 * nn);
+    for (int k = 0; k < K; ++k) {
+        const double* X = x + (size_t)k * nn;
+        const double* Y = y + (size_t)k * nn;
+        const double* Bk = b + (size_t)k * nn;
+        double vol = 0.0;
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double x_xi = 0, x_eta = 0, y_xi = 0, y_eta = 0;
+                for (int q = 0; q < n; ++q) {
+                    x_xi += D[i * n + q] * X[j * n + q];
+                    y_xi += D[i * n + q] * Y[j * n + q];
+                    x_eta += D[j * n + q] * X[q * n + i];
+                    y_eta += D[j * n + q] * Y[q * n + i];
+                }
+                const double J = x_xi * y_eta - x_eta * y_xi;
+                const long long id = (long long)k * nn + j * n + i;
+                if (!(J > 0.0) || !isfinite(J))
+                    return fail(SWE_ERR_GEOM, "swe_create: non-positive Jacobian in element " + std::to_string(k));
+                axx[id] = y_eta;
+                axy[id] = -x_eta;
+                aex[id] = -y_xi;
+                aey[id] = x_xi;
+                Jv[id] = J;
+                rJ[id] = 1.0 / J;
+                wJ[id] = w[i] * w[j] * J;
+                vol += wJ[id];
+                bn[id] = Bk[j * n + i];
+                cfln[id] = (sqrt(y_eta * y_eta + x_eta * x_eta) + sqrt(y_xi * y_xi + x_xi * x_xi)) / J;
+            }
+        rvol[k] = 1.0 / vol;
+        // split-form bathymetry derivatives (Eq. SourceDisc, plain D):
+        // gamma_c = a_xi,c D_xi b + D_xi(a_xi,c b) + a_eta,c D_eta b + D_eta(a_eta,c b)
+        const long long o = (long long)k * nn;
+        for (int a = 0; a < nn; ++a) {
+            tmp[a] = axx[o + a] * bn[o + a];
+            tmp[nn + a] = aex[o + a] * bn[o + a];
+            tmp[2 * nn + a] = axy[o + a] * bn[o + a];
+            tmp[3 * nn + a] = aey[o + a] * bn[o + a];
+        }
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                double bx = 0, be = 0, d0 = 0, d1 = 0, d2 = 0, d3 = 0;
+                for (int q = 0; q < n; ++q) {
+                    bx += D[i * n + q] * bn[o + j * n + q];
+                    be += D[j * n + q] * bn[o + q * n + i];
+                    d0 += D[i * n + q] * tmp[j * n + q];
+                    d1 += D[j * n + q] * tmp[nn + q * n + i];
+                    d2 += D[i * n + q] * tmp[2 * nn + j * n + q];
+                    d3 += D[j * n + q] * tmp[3 * nn + q * n + i];
+                }
+                const long long id = o + j * n + i;
+                const double gx = axx[id] * bx + d0 + aex[id] * be + d1;
+                const double gy = axy[id] * bx + d2 + aey[id] * be + d3;
+                srcx[id] = -0.5 * g * gx * rJ[id];
+                srcy[id] = -0.5 * g * gy * rJ[id];
+            }
+    }
+
+    // ---- unique faces and element sides ----
+    std::vector<int32_t> f_im, f_ip, f_tm, f_tp, s_nb(KS);
+    std::vector<double> f_nx, f_ny, f_js, f_bm, f_bp, s_nx(KS), s_ny(KS), s_rwa(KS);
+    const double w0 = w[0];
+    auto outward = [&](int k, int f, int i, int j, double& nx, double& ny) {
+        const long long id = (long long)k * nn + j * n + i;
+        switch (f) {
+            case 0: nx = -aex[id]; ny = -aey[id]; break;
+            case 1: nx = axx[id]; ny = axy[id]; break;
+            case 2: nx = aex[id]; ny = aey[id]; break;
+            default: nx = -axx[id]; ny = -axy[id]; break;
+        }
+    };
+    int nfaces = 0;
+    for (int k = 0; k < K; ++k)
+        for (int f = 0; f < 4; ++f) {
+            const int kk = EToE[4 * k + f], ff = EToF[4 * k + f], fl = flip[4 * k + f];
+            for (int pn = 0; pn < n; ++pn) {
+                const int q = fl ? N - pn : pn;
+                int i, j, ii, jj;
+                face_node(N, f, pn, i, j);
+                face_node(N, ff, q, ii, jj);
+                const long long own = (long long)k * nn + j * n + i;
+                const long long nb = (long long)kk * nn + jj * n + ii;
+                double nx, ny;
+                outward(k, f, i, j, nx, ny);
+                const double js = sqrt(nx * nx + ny * ny);
+                const long long slot = ((long long)k * 4 + f) * n + pn;
+                s_nb[slot] = (int32_t)nb;
+                s_nx[slot] = nx / js;
+                s_ny[slot] = ny / js;
+                s_rwa[slot] = js / (w0 * Jv[own]);
+                if (kk > k || (kk == k && ff > f)) {
+                    f_im.push_back((int32_t)own);
+                    f_ip.push_back((int32_t)nb);
+                    f_tm.push_back((int32_t)slot);
+                    f_tp.push_back((int32_t)(((long long)kk * 4 + ff) * n + q));
+                    f_nx.push_back(nx / js);
+                    f_ny.push_back(ny / js);
+                    f_js.push_back(js);
+                    f_bm.push_back(bn[own]);
+                    f_bp.push_back(bn[nb]);
+                }
+            }
+            if (kk > k || (kk == k && ff > f)) ++nfaces;
+        }
+
+    // ---- device ----
+    swe_ctx* c = new swe_ctx();
+    cudaError_t err = cudaGetDevice(&c->device);
+    if (err != cudaSuccess) {
+        delete c;
+        return cuda_fail(err, "swe_create: cudaGetDevice");
+    }
+    init_device_tables(c->device);
+    c->p = *p;
+    const double s0 = -4.0 * log10((double)N);
+    c->sigma_min = isnan(p->sigma_min) ? s0 - 1.0 : p->sigma_min;
+    c->sigma_max = isnan(p->sigma_max) ? s0 + 1.0 : p->sigma_max;
+    c->h_tol = isnan(p->h_tol) ? 1e-4 : p->h_tol;
+    DeviceMesh& m = c->m;
+    m.N = N;
+    m.n = n;
+    m.K = K;
+    m.nfaces = nfaces;
+    m.KN = KN;
+    m.KS = KS;
+    m.g = g;
+    cudaError_t e2 = cudaSuccess;
+#define UP(dst, src)                                  \
+    dst = dev_upload(c, src, e2);                     \
+    if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: upload"); }
+    UP(m.axx, axx) UP(m.axy, axy) UP(m.aex, aex) UP(m.aey, aey) UP(m.rJ, rJ) UP(m.wJ, wJ)
+    UP(m.srcx, srcx) UP(m.srcy, srcy) UP(m.bn, bn) UP(m.nax, cfln) UP(m.rvol, rvol)
+    UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
+    UP(m.f_ny, f_ny) UP(m.f_js, f_js) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
+    UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
+#undef UP
+    m.nae = nullptr;
+    Work& W = c->w;
+#define AL(dst, count)                                \
+    dst = dev_alloc(c, count, e2);                    \
+    if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
+    AL(W.uv, 2 * KN) AL(W.Fout, 3 * KS) AL(W.Ustar, 2 * KS) AL(W.eps, K) AL(W.Kreg, 3 * KN)
+    AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 3 * 608 + 8) AL(W.dt, 4)
+    if (p->av) {
+        AL(W.Fvt, 4 * KN) AL(W.Fvtr, 4 * KS) AL(W.Fvout, 2 * KS)
+    }
+#undef AL
+    {
+        void* q = nullptr;
+        e2 = cudaMalloc(&q, 2 * sizeof(unsigned long long) + 16);
+        if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
+        c->allocations.push_back(q);
+        W.dtbits = static_cast<unsigned long long*>(q);
+        W.status = reinterpret_cast<int*>(static_cast<char*>(q) + 2 * sizeof(unsigned long long));
+    }
+    cudaMemset(W.status, 0, sizeof(int));
+    cudaMemset(W.eps, 0, sizeof(double) * K);
+    e2 = cudaDeviceSynchronize();
+    if (e2 != cudaSuccess) {
+        free_all(c);
+        delete c;
+        return cuda_fail(e2, "swe_create");
+    }
+    *out = c;
+    return SWE_OK;
+}
+
+extern "C" void swe_destroy(swe_ctx* c) {
+    if (!c) return;
+    cudaDeviceSynchronize();
+    free_all(c);
+    delete c;
+}
+
+// ---------------------------------------------------------------------------
+// Right-hand side
+// ---------------------------------------------------------------------------
+
+namespace {
+
+void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done) {
+    if (!prim_done) swe::launch_prim(c, W, s, stop);
+    swe::launch_surface(c, W, s, stop);
+    if (c->p.av) {
+        swe::launch_av(c, W, s, stop);
+        swe::launch_visc_face(c, s, stop);
+    }
+    swe::launch_volume(c, W, R, s, stop);
+}
+
+int check_launch(const char* where) {
+    cudaError_t e = cudaGetLastError();
+    return e == cudaSuccess ? SWE_OK : cuda_fail(e, where);
+}
+
+}  // namespace
+
+extern "C" int swe_rhs(swe_ctx* c, const double* W, double* R, void* stream) {
+    if (!c || !W || !R) return fail(SWE_ERR_ARG, "swe_rhs: NULL argument");
+    if (W == R) return fail(SWE_ERR_ARG, "swe_rhs: W and R must not overlap");
+    rhs_chain(c, W, R, (cudaStream_t)stream, nullptr, false);
+    return check_launch("swe_rhs");
+}
+
+extern "C" int swe_limit(swe_ctx* c, double* W, void* stream) {
+    if (!c || !W) return fail(SWE_ERR_ARG, "swe_limit: NULL argument");
+    swe_params saved = c->p;
+    c->p.limiter = 1;
+    swe::launch_update(c, 0, W, 0.0, 0.0, 0.0, nullptr, (cudaStream_t)stream, nullptr);
+    c->p = saved;
+    return check_launch("swe_limit");
+}
+
+extern "C" int swe_max_dt(swe_ctx* c, const double* W, double* dt_cfl, double* dt_pos, void* stream) {
+    if (!c || !W) return fail(SWE_ERR_ARG, "swe_max_dt: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    swe::launch_prim(c, W, s, nullptr);
+    swe::launch_dt(c, W, 0.0, s, nullptr);
+    double h[4];
+    cudaMemcpyAsync(h, c->w.dt, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_max_dt");
+    if (dt_cfl) *dt_cfl = h[1];
+    if (dt_pos) *dt_pos = h[2];
+    return check_launch("swe_max_dt");
+}
+
+extern "C" int swe_step(swe_ctx* c, double* W, double dt, int nsteps, double* dt_last, void* stream) {
+    if (!c || !W || nsteps < 0) return fail(SWE_ERR_ARG, "swe_step: bad argument");
+    if (!(dt > 0.0) && !(c->p.cfl > 0.0)) return fail(SWE_ERR_ARG, "swe_step: dt <= 0 needs cfl > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int* stop = c->w.status;
+    const long long n3 = 3 * c->m.KN;
+    const bool adaptive = !(dt > 0.0);
+    const double* dtd = adaptive ? c->w.dt : nullptr;
+    cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+    for (int st = 0; st < nsteps; ++st) {
+        swe::launch_copy(c, W, c->w.Wn, n3, s, stop);
+        bool prim_done = false;
+        if (adaptive) {
+            swe::launch_prim(c, W, s, stop);
+            swe::launch_dt(c, W, 0.0, s, stop);
+            prim_done = true;
+        }
+        if (c->p.rk == 0) {
+            for (int stage = 0; stage < 5; ++stage) {
+                rhs_chain(c, W, c->w.R, s, stop, prim_done && stage == 0);
+                swe::launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop);
+            }
+        } else {
+            const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+            for (int stage = 0; stage < 3; ++stage) {
+                rhs_chain(c, W, c->w.R, s, stop, prim_done && stage == 0);
+                swe::launch_update(c, 2, W, ca[stage], cb[stage], dt, dtd, s, stop);
+            }
+        }
+    }
+    int rc = check_launch("swe_step");
+    if (rc) return rc;
+    int status = 0;
+    double dth = dt;
+    cudaMemcpyAsync(&status, c->w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (adaptive) cudaMemcpyAsync(&dth, c->w.dt, sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_step");
+    if (dt_last) *dt_last = dth;
+    if (status) {
+        cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+        cudaMemcpyAsync(W, c->w.Wn, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_step: rollback");
+        if (status & 2) return fail(SWE_ERR_NONFINITE, "swe_step: non-finite state; rolled back the failing step");
+        return fail(SWE_ERR_NEG_MEAN, "swe_step: negative element mean water height; rolled back the failing step");
+    }
+    return SWE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics, status, timing
+// ---------------------------------------------------------------------------
+
+extern "C" int swe_mass(swe_ctx* c, const double* W, double* out3, void* stream) {
+    if (!c || !W || !out3) return fail(SWE_ERR_ARG, "swe_mass: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double h[3];
+    swe::launch_reduce(c, W, 0, h, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_mass");
+    for (int i = 0; i < 3; ++i) out3[i] = h[i];
+    return check_launch("swe_mass");
+}
+
+extern "C" int swe_entropy(swe_ctx* c, const double* W, double* E, void* stream) {
+    if (!c || !W || !E) return fail(SWE_ERR_ARG, "swe_entropy: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double h[3];
+    swe::launch_reduce(c, W, 1, h, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_entropy");
+    *E = h[0];
+    return check_launch("swe_entropy");
+}
+
+extern "C" int swe_get_epsilon(swe_ctx* c, double* eps, void* stream) {
+    if (!c || !eps) return fail(SWE_ERR_ARG, "swe_get_epsilon: NULL argument");
+    cudaError_t e = cudaMemcpyAsync(eps, c->w.eps, sizeof(double) * c->m.K, cudaMemcpyDeviceToDevice,
+                                    (cudaStream_t)stream);
+    return e == cudaSuccess ? SWE_OK : cuda_fail(e, "swe_get_epsilon");
+}
+
+extern "C" int swe_status(swe_ctx* c, int* bits, void* stream) {
+    if (!c || !bits) return fail(SWE_ERR_ARG, "swe_status: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    int v = 0;
+    cudaMemcpyAsync(&v, c->w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_status");
+    *bits = v;
+    return SWE_OK;
+}
+
+extern "C" int swe_timing(swe_ctx* c, int on) {
+    if (!c) return fail(SWE_ERR_ARG, "swe_timing: NULL context");
+    if (on && c->ev.empty()) {
+        c->ev.resize(2 * kEventPairs);
+        c->ev_class.assign(kEventPairs, -1);
+        for (auto& e : c->ev) {
+            cudaError_t r = cudaEventCreate(&e);
+            if (r != cudaSuccess) return cuda_fail(r, "swe_timing");
+        }
+    }
+    c->timing = on != 0;
+    c->ev_used = 0;
+    return SWE_OK;
+}
+
+extern "C" int swe_timing_read(swe_ctx* c, int which, double* ms, int64_t* launches) {
+    if (!c || !ms || !launches) return fail(SWE_ERR_ARG, "swe_timing_read: NULL argument");
+    double tot = 0.0;
+    int64_t cnt = 0;
+    for (int i = 0; i < c->ev_used; ++i) {
+        if (c->ev_class[i] != which) continue;
+        cudaError_t e = cudaEventSynchronize(c->ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_timing_read");
+        float t = 0.f;
+        e = cudaEventElapsedTime(&t, c->ev[2 * i], c->ev[2 * i + 1]);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_timing_read");
+        tot += t;
+        ++cnt;
+    }
+    *ms = tot;
+    *launches = cnt;
+    return SWE_OK;
+}
+
+extern "C" int64_t swe_launches(const swe_ctx* c) { return c ? c->launches : 0; }
+
+extern "C" int swe_info(const swe_ctx* c, int* N, int* K, int* nfaces) {
+    if (!c) return fail(SWE_ERR_ARG, "swe_info: NULL context");
+    if (N) *N = c->m.N;
+    if (K) *K = c->m.K;
+    if (nfaces) *nfaces = c->m.nfaces;
+    return SWE_OK;
+}
+
+extern "C" const char* swe_last_error(void) { return g_last_error.c_str(); }

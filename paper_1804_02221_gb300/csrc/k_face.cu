@@ -1,0 +1,463 @@
+// Node-, face- and element-wise kernels other than the volume term:
+// primitives, the entropy-stable interface flux, the BR1 viscous interface
+// average, the fused Runge-Kutta stage update with the positivity limiter,
+// the time-step reduction and the diagnostic integrals.
+#include <math.h>
+
+#include "kcommon.cuh"
+
+namespace swe {
+namespace {
+
+// ---------------------------------------------------------------------------
+// Primitive velocities u = hu/h, v = hv/h (zero where h <= 0): one reciprocal
+// per node, reused by every later kernel of the stage.
+// ---------------------------------------------------------------------------
+__global__ void k_prim(long long KN, const double* __restrict__ W, double* __restrict__ uv,
+                       const int* stop) {
+    if (stopped(stop)) return;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < KN;
+         id += (long long)gridDim.x * blockDim.x) {
+        const double h = W[id];
+        const double rh = h > 0.0 ? 1.0 / h : 0.0;
+        uv[id] = W[KN + id] * rh;
+        uv[KN + id] = W[2 * KN + id] * rh;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Interface flux through the owner's outward normal at every unique face
+// node (Eq. NumericalSurfaceFlux evaluated in the normal frame, App. B):
+// rotate the velocities (Eq. rotatingVelocities), EC flux of Eq.
+// surfaceFluxes, minus 1/2 R~|Lambda~|R~^T [[q~]] (Eqs. fesandges,
+// RightEigenvectors2DCurved, ScalingMatrix2DCurved), rotate back (Eq.
+// surfaceFlux2DRotated), times the surface Jacobian. With [[a^2]] = 2{a}[[a]]
+// the projection R~^T [[q~]] is (g[[h+b]] + {c}[[u~]], [[v~]],
+// g[[h+b]] - {c}[[u~]]). Writes +F to the owner's side slot and -F to the
+// neighbour's, and the BR1 interface values {u}, {v} to both.
+// ---------------------------------------------------------------------------
+template <bool ES>
+__global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const double* __restrict__ uv,
+                          double* __restrict__ Fout, double* __restrict__ Ustar, const int* stop) {
+    if (stopped(stop)) return;
+    const long long total = (long long)m.nfaces * m.n;
+    const double g = m.g;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long im = m.f_im[t], ip = m.f_ip[t], tm = m.f_tm[t], tp = m.f_tp[t];
+        const double nx = m.f_nx[t], ny = m.f_ny[t], js = m.f_js[t];
+        const double hm = W[im], hp = W[ip];
+        const double um = uv[im], vm = uv[m.KN + im], up = uv[ip], vp = uv[m.KN + ip];
+        const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
+        const double utp = fma(nx, up, ny * vp), vtp = fma(nx, vp, -ny * up);
+        const double ha = 0.5 * (hm + hp), ua = 0.5 * (utm + utp), va = 0.5 * (vtm + vtp);
+        const double h2a = 0.5 * fma(hm, hm, hp * hp);
+        double F1 = ha * ua;
+        double F2 = fma(F1, ua, 0.5 * g * h2a);
+        double F3 = F1 * va;
+        if (ES) {
+            const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
+            const double gH = g * ((hp + m.f_bp[t]) - (hm + m.f_bm[t]));
+            const double dut = utp - utm, dvt = vtp - vtm;
+            const double r2g = 0.5 / g;
+            const double s1 = fabs(ua + ca) * r2g * fma(ca, dut, gH);
+            const double s3 = fabs(ua - ca) * r2g * fma(-ca, dut, gH);
+            const double d1 = s1 + s3;
+            F1 = fma(-0.5, d1, F1);
+            F2 = fma(-0.5, fma(ua, d1, ca * (s1 - s3)), F2);
+            F3 = fma(-0.5, fma(va, d1, fabs(ha * ua) * dvt), F3);
+        }
+        const double G1 = js * F1;
+        const double G2 = js * fma(nx, F2, -ny * F3);
+        const double G3 = js * fma(ny, F2, nx * F3);
+        Fout[tm] = G1;
+        Fout[m.KS + tm] = G2;
+        Fout[2 * m.KS + tm] = G3;
+        Fout[tp] = -G1;
+        Fout[m.KS + tp] = -G2;
+        Fout[2 * m.KS + tp] = -G3;
+        const double us = 0.5 * (um + up), vs = 0.5 * (vm + vp);
+        Ustar[tm] = us;
+        Ustar[m.KS + tm] = vs;
+        Ustar[tp] = us;
+        Ustar[m.KS + tp] = vs;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// BR1 viscous interface flux {F^v . n} (Thm. 1) with the owner's unscaled
+// outward normal; +avg to the owner's slot, -avg to the neighbour's.
+// ---------------------------------------------------------------------------
+__global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, double* __restrict__ Fvout,
+                            const int* stop) {
+    if (stopped(stop)) return;
+    const long long total = (long long)m.nfaces * m.n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long tm = m.f_tm[t], tp = m.f_tp[t];
+        const double nx = m.f_nx[t] * m.f_js[t], ny = m.f_ny[t] * m.f_js[t];
+        const long long S = m.KS;
+        const double a2 = 0.5 * fma(nx, Fvtr[tm] + Fvtr[tp], ny * (Fvtr[2 * S + tm] + Fvtr[2 * S + tp]));
+        const double a3 = 0.5 * fma(nx, Fvtr[S + tm] + Fvtr[S + tp], ny * (Fvtr[3 * S + tm] + Fvtr[3 * S + tp]));
+        Fvout[tm] = a2;
+        Fvout[S + tm] = a3;
+        Fvout[tp] = -a2;
+        Fvout[S + tp] = -a3;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Runge-Kutta stage update fused with the positivity limiter (Eq. PosPres)
+// and the h_tol momentum cut; one warp per element, deterministic butterfly
+// reductions. MODE 0: limiter only; 1: 2N-storage stage K = a K + dt R,
+// W = W + b K (K = dt R when a = 0); 2: SSP stage W = a Wn + b (W + dt R).
+// ---------------------------------------------------------------------------
+struct UpdArgs {
+    DeviceMesh m;
+    double* W;
+    const double* R;
+    double* Kreg;
+    const double* Wn;
+    double a, b, dt_host;
+    const double* dt_dev;
+    int limiter;
+    double h_tol;
+    int* status;
+    const int* stop;
+};
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int N, int MODE>
+__global__ void k_update(UpdArgs a) {
+    constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
+    if (stopped(a.stop)) return;
+    const DeviceMesh& m = a.m;
+    const int lane = threadIdx.x & 31;
+    const long long k = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= m.K) return;
+    const long long KN = m.KN;
+    const double dt = a.dt_dev ? *a.dt_dev : a.dt_host;
+    double h[PER], hu[PER], hv[PER];
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int node = lane + 32 * r;
+        h[r] = hu[r] = hv[r] = 0.0;
+        if (node < nn) {
+            const long long gid = k * nn + node;
+            double w0 = a.W[gid], w1 = a.W[KN + gid], w2 = a.W[2 * KN + gid];
+            if (MODE == 1) {
+                const double r0 = dt * a.R[gid], r1 = dt * a.R[KN + gid], r2 = dt * a.R[2 * KN + gid];
+                double k0v = r0, k1v = r1, k2v = r2;
+                if (a.a != 0.0) {
+                    k0v = fma(a.a, a.Kreg[gid], r0);
+                    k1v = fma(a.a, a.Kreg[KN + gid], r1);
+                    k2v = fma(a.a, a.Kreg[2 * KN + gid], r2);
+                }
+                a.Kreg[gid] = k0v;
+                a.Kreg[KN + gid] = k1v;
+                a.Kreg[2 * KN + gid] = k2v;
+                w0 = fma(a.b, k0v, w0);
+                w1 = fma(a.b, k1v, w1);
+                w2 = fma(a.b, k2v, w2);
+            } else if (MODE == 2) {
+                const double s0 = fma(dt, a.R[gid], w0), s1 = fma(dt, a.R[KN + gid], w1),
+                             s2 = fma(dt, a.R[2 * KN + gid], w2);
+                w0 = fma(a.a, a.Wn[gid], a.b * s0);
+                w1 = fma(a.a, a.Wn[KN + gid], a.b * s1);
+                w2 = fma(a.a, a.Wn[2 * KN + gid], a.b * s2);
+            }
+            h[r] = w0;
+            hu[r] = w1;
+            hv[r] = w2;
+        }
+    }
+    if (a.limiter) {
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, mn = INFINITY;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int node = lane + 32 * r;
+            if (node < nn) {
+                const double wj = m.wJ[k * nn + node];
+                s0 = fma(wj, h[r], s0);
+                s1 = fma(wj, hu[r], s1);
+                s2 = fma(wj, hv[r], s2);
+                mn = fmin(mn, h[r]);
+            }
+        }
+        const double rv = m.rvol[k];
+        const double m0 = warp_sum(s0) * rv, m1 = warp_sum(s1) * rv, m2 = warp_sum(s2) * rv;
+        mn = warp_min(mn);
+        bool ok = true;
+        if (!isfinite(m0) || !isfinite(m1) || !isfinite(m2)) {
+            if (lane == 0) atomicOr(a.status, 2);
+            ok = false;
+        } else if (m0 < 0.0) {
+            if (lane == 0) atomicOr(a.status, 1);
+            ok = false;
+        }
+        if (ok) {
+            if (mn < 0.0 && m0 - mn > 0.0) {
+                const double theta = fmin(1.0, m0 / (m0 - mn));
+#pragma unroll
+                for (int r = 0; r < PER; ++r) {
+                    h[r] = fma(theta, h[r] - m0, m0);
+                    hu[r] = fma(theta, hu[r] - m1, m1);
+                    hv[r] = fma(theta, hv[r] - m2, m2);
+                }
+            }
+#pragma unroll
+            for (int r = 0; r < PER; ++r)
+                if (h[r] < a.h_tol) hu[r] = hv[r] = 0.0;
+        }
+    } else if (a.status != nullptr && MODE != 0) {
+        double s0 = 0.0;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) s0 += fabs(h[r]) + fabs(hu[r]) + fabs(hv[r]);
+        s0 = warp_sum(s0);
+        if (!isfinite(s0) && lane == 0) atomicOr(a.status, 2);
+    }
+#pragma unroll
+    for (int r = 0; r < PER; ++r) {
+        const int node = lane + 32 * r;
+        if (node < nn) {
+            const long long gid = k * nn + node;
+            a.W[gid] = h[r];
+            a.W[KN + gid] = hu[r];
+            a.W[2 * KN + gid] = hv[r];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Time step: max over nodes of (lambda_xi + lambda_eta)/J and max over element
+// side nodes of the inverse positivity restrictions of Eq. CFLConstraints
+// (Lemma PosPres), reduced with integer atomics on the bit patterns of
+// non-negative doubles; one warp per element.
+// ---------------------------------------------------------------------------
+struct DtArgs {
+    DeviceMesh m;
+    const double* W;
+    const double* uv;
+    const double* cfl_n;
+    int pos;
+    unsigned long long* bits;
+    const int* stop;
+};
+
+template <int N>
+__global__ void k_dt(DtArgs a) {
+    constexpr int n = N + 1, nn = n * n;
+    if (stopped(a.stop)) return;
+    const DeviceMesh& m = a.m;
+    const int lane = threadIdx.x & 31;
+    const long long k = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (k >= m.K) return;
+    const double g = m.g;
+    double lam = 0.0;
+    for (int node = lane; node < nn; node += 32) {
+        const long long id = k * nn + node;
+        const double h = a.W[id], u = a.uv[id], v = a.uv[m.KN + id];
+        const double c = sqrt(g * fmax(h, 0.0));
+        const double vel = fabs(fma(m.axx[id], u, m.axy[id] * v)) + fabs(fma(m.aex[id], u, m.aey[id] * v));
+        lam = fmax(lam, fma(c, a.cfl_n[id], m.rJ[id] * vel));
+    }
+    lam = warp_max(lam);
+    if (lane == 0 && lam > 0.0) atomic_max_pos(&a.bits[0], lam);
+    if (!a.pos) return;
+    double inv = 0.0;
+    for (int sn = lane; sn < 4 * n; sn += 32) {
+        const int f = sn / n, p = sn - f * n;
+        const int i = (f == 0 || f == 2) ? p : (f == 1 ? N : 0);
+        const int j = (f == 1 || f == 3) ? p : (f == 2 ? N : 0);
+        const long long own = k * nn + j * n + i;
+        const long long slot = k * 4 * n + sn;
+        const long long nb = m.s_nb[slot];
+        const double nx = m.s_nx[slot], ny = m.s_ny[slot], rwa = m.s_rwa[slot];
+        const double hm = a.W[own], hp = a.W[nb];
+        const double utm = fma(nx, a.uv[own], ny * a.uv[m.KN + own]);
+        const double utp = fma(nx, a.uv[nb], ny * a.uv[m.KN + nb]);
+        const double ua = 0.5 * (utm + utp);
+        const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
+        const double ap = fabs(ua + ca), am = fabs(ua - ca);
+        const double A = ap + am, B = ap - am;
+        const double i1 = fma(2.0, ua, A) * rwa;
+        if (i1 > 0.0) inv = fmax(inv, i1);
+        const double jump = utp - utm;
+        if (hm > 0.0 && B * jump < 0.0) inv = fmax(inv, fabs(ca * B * jump) * rwa / (g * hm));
+    }
+    inv = warp_max(inv);
+    if (lane == 0 && inv > 0.0) atomic_max_pos(&a.bits[1], inv);
+}
+
+__global__ void k_dt_final(const unsigned long long* bits, double* dt, double cfl, int N,
+                           double dt_fixed, const int* stop) {
+    if (stopped(stop)) return;
+    const double lam = __longlong_as_double((long long)bits[0]);
+    const double inv = __longlong_as_double((long long)bits[1]);
+    const double dtc = lam > 0.0 ? cfl * 2.0 / (N + 1.0) / lam : INFINITY;
+    const double dtp = inv > 0.0 ? 1.0 / inv : INFINITY;
+    dt[1] = dtc;
+    dt[2] = dtp;
+    dt[0] = dt_fixed > 0.0 ? dt_fixed : fmin(dtc, dtp);
+}
+
+__global__ void k_copy(long long count, const double* __restrict__ src, double* __restrict__ dst,
+                       const int* stop) {
+    if (stopped(stop)) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: sum J w w W (what = 0, three sums) or sum J w w e(W) (what = 1,
+// Eq. entropyFunction). Fixed grid, per-block tree sums, then one block adds
+// the partials in order: the result does not depend on scheduling.
+// ---------------------------------------------------------------------------
+constexpr int RED_BLOCKS = 608;
+constexpr int RED_THREADS = 256;
+
+__global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int what,
+                              double* __restrict__ part) {
+    __shared__ double sh[3][RED_THREADS];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    const double g = m.g;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < m.KN;
+         id += (long long)gridDim.x * blockDim.x) {
+        const double wj = m.wJ[id], h = W[id], hu = W[m.KN + id], hv = W[2 * m.KN + id];
+        if (what == 0) {
+            s0 = fma(wj, h, s0);
+            s1 = fma(wj, hu, s1);
+            s2 = fma(wj, hv, s2);
+        } else {
+            const double kin = h > 0.0 ? 0.5 * fma(hu, hu, hv * hv) / h : 0.0;
+            const double e = kin + g * h * fma(0.5, h, m.bn[id]);
+            s0 = fma(wj, e, s0);
+        }
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    sh[2][threadIdx.x] = s2;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+        for (int c = 0; c < 3; ++c) part[c * RED_BLOCKS + blockIdx.x] = sh[c][0];
+}
+
+__global__ void k_reduce_final(const double* __restrict__ part, double* __restrict__ out) {
+    if (threadIdx.x < 3) {
+        double s = 0.0;
+        for (int b = 0; b < RED_BLOCKS; ++b) s += part[threadIdx.x * RED_BLOCKS + b];
+        out[threadIdx.x] = s;
+    }
+}
+
+template <int N>
+void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
+    constexpr int WPB = 4;
+    const int blocks = grid_for(c->m.K, WPB);
+    Timed tm(c, KC_UPDATE, s);
+    if (mode == 0) k_update<N, 0><<<blocks, 32 * WPB, 0, s>>>(a);
+    else if (mode == 1) k_update<N, 1><<<blocks, 32 * WPB, 0, s>>>(a);
+    else k_update<N, 2><<<blocks, 32 * WPB, 0, s>>>(a);
+}
+
+template <int N>
+void dt_n(swe_ctx* c, const DtArgs& a, cudaStream_t s) {
+    constexpr int WPB = 4;
+    Timed tm(c, KC_DT, s);
+    k_dt<N><<<grid_for(c->m.K, WPB), 32 * WPB, 0, s>>>(a);
+}
+
+#define SWE_SWITCH_N(N, CALL)                                                         \
+    switch (N) {                                                                      \
+        case 1: CALL(1); break; case 2: CALL(2); break; case 3: CALL(3); break;      \
+        case 4: CALL(4); break; case 5: CALL(5); break; case 6: CALL(6); break;      \
+        case 7: CALL(7); break; case 8: CALL(8); break; case 9: CALL(9); break;      \
+        case 10: CALL(10); break; case 11: CALL(11); break; case 12: CALL(12); break; \
+        default: break;                                                               \
+    }
+
+}  // namespace
+
+void init_tables_face() { upload_tables(); }
+
+void launch_prim(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
+    Timed tm(c, KC_PRIM, s);
+    k_prim<<<grid_for(c->m.KN, 256), 256, 0, s>>>(c->m.KN, W, c->w.uv, stop);
+}
+
+void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
+    const long long total = (long long)c->m.nfaces * c->m.n;
+    Timed tm(c, KC_FACE, s);
+    if (c->p.flux)
+        k_surface<true><<<grid_for(total, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
+    else
+        k_surface<false><<<grid_for(total, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
+}
+
+void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop) {
+    const long long total = (long long)c->m.nfaces * c->m.n;
+    Timed tm(c, KC_VFACE, s);
+    k_visc_face<<<grid_for(total, 128), 128, 0, s>>>(c->m, c->w.Fvtr, c->w.Fvout, stop);
+}
+
+void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,
+                   const double* dt_dev, cudaStream_t s, const int* stop) {
+    UpdArgs u{c->m, W, c->w.R, c->w.Kreg, c->w.Wn, a, b, dt_host, dt_dev, c->p.limiter,
+              c->h_tol, c->w.status, stop};
+#define SWE_UPD(NN) update_n<NN>(c, mode, u, s)
+    SWE_SWITCH_N(c->m.N, SWE_UPD)
+#undef SWE_UPD
+}
+
+void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, const int* stop) {
+    cudaMemsetAsync(c->w.dtbits, 0, 2 * sizeof(unsigned long long), s);
+    DtArgs a{c->m, W, c->w.uv, c->m.nax, (c->p.limiter && c->p.flux) ? 1 : 0, c->w.dtbits, stop};
+#define SWE_DT(NN) dt_n<NN>(c, a, s)
+    SWE_SWITCH_N(c->m.N, SWE_DT)
+#undef SWE_DT
+    Timed tm(c, KC_DT, s);
+    k_dt_final<<<1, 1, 0, s>>>(c->w.dtbits, c->w.dt, c->p.cfl, c->m.N, dt_fixed, stop);
+}
+
+void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
+                 const int* stop) {
+    Timed tm(c, KC_UPDATE, s);
+    k_copy<<<grid_for(count, 256) > 4096 ? 4096 : grid_for(count, 256), 256, 0, s>>>(count, src, dst, stop);
+}
+
+void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cudaStream_t s) {
+    {
+        Timed tm(c, KC_REDUCE, s);
+        k_reduce_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->m, W, what, c->w.part);
+    }
+    {
+        Timed tm(c, KC_REDUCE, s);
+        k_reduce_final<<<1, 32, 0, s>>>(c->w.part, c->w.part + 3 * RED_BLOCKS);
+    }
+    cudaMemcpyAsync(host_out, c->w.part + 3 * RED_BLOCKS, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+}  // namespace swe

@@ -1,0 +1,160 @@
+// Internal declarations of the swedg library (host side).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "../../include/swedg.h"
+
+namespace swe {
+
+constexpr int NMAX = SWE_NMAX;
+constexpr int NFACE = 4;
+
+// Basis of degree N on LGL nodes (Sec. 2.2) and the inverse Vandermonde
+// matrix of the normalised Legendre polynomials (App. A), row-major n x n.
+struct Basis {
+    int N = 0;
+    std::vector<double> xi, w, D, Vinv;
+};
+Basis make_basis(int N);
+
+// Offsets of degree N's tables inside the packed constant arrays.
+constexpr int mat_offset(int N) {  // sum_{M<N} (M+1)^2
+    int s = 0;
+    for (int M = 1; M < N; ++M) s += (M + 1) * (M + 1);
+    return s;
+}
+constexpr int vec_offset(int N) {  // sum_{M<N} (M+1)
+    int s = 0;
+    for (int M = 1; M < N; ++M) s += M + 1;
+    return s;
+}
+constexpr int MAT_TOTAL = mat_offset(NMAX + 1);
+constexpr int VEC_TOTAL = vec_offset(NMAX + 1);
+
+// Packed tables of all degrees 1..NMAX (D, Vinv, w), filled once per process.
+struct Tables {
+    double D[MAT_TOTAL];
+    double Vinv[MAT_TOTAL];
+    double w[VEC_TOTAL];
+};
+const Tables& tables();
+
+// Kernel classes for timing.
+enum KernelClass {
+    KC_VOLUME = 0,
+    KC_FACE = 1,
+    KC_PRIM = 2,
+    KC_AV = 3,
+    KC_VFACE = 4,
+    KC_UPDATE = 5,
+    KC_DT = 6,
+    KC_REDUCE = 7,
+    KC_COUNT = 8
+};
+
+// Device-side data of one context. Nodal arrays are [K][n][n] planes,
+// side arrays [K][4][n] (element side node), face arrays [nfaces][n].
+struct DeviceMesh {
+    int N, n, K, nfaces;
+    long long KN;       // K*n*n
+    long long KS;       // K*4*n
+    double g;
+    // per node
+    const double* axx;  // contravariant xi vector (y_eta, -x_eta)
+    const double* axy;
+    const double* aex;  // contravariant eta vector (-y_xi, x_xi)
+    const double* aey;
+    const double* rJ;   // 1/J
+    const double* wJ;   // w_i w_j J
+    const double* srcx; // -(g/2) gamma_x / J  (source of the x momentum is h*srcx)
+    const double* srcy; // -(g/2) gamma_y / J
+    const double* bn;   // bathymetry
+    const double* nax;  // |a_xi| / J
+    const double* nae;  // |a_eta| / J
+    const double* rvol; // [K] 1 / sum_ij w_i w_j J
+    // per unique face node
+    const int32_t* f_im;   // owner node id (k*n*n + j*n + i)
+    const int32_t* f_ip;   // neighbour node id
+    const int32_t* f_tm;   // owner side slot ((k*4+f)*n + p)
+    const int32_t* f_tp;   // neighbour side slot
+    const double* f_nx;    // owner outward unit normal
+    const double* f_ny;
+    const double* f_js;    // surface Jacobian |outward unscaled normal|
+    const double* f_bm;    // bathymetry on both sides
+    const double* f_bp;
+    // per element side node
+    const int32_t* s_nb;   // node id of the neighbour's matching node
+    const double* s_nx;    // own outward unit normal
+    const double* s_ny;
+    const double* s_rwa;   // 1/(omega_0 a), a = J/Jsurf (Lemma PosPres)
+};
+
+struct Work {
+    double* uv;     // [2][KN] velocities
+    double* Fout;   // [3][KS] outward interface flux (x Jsurf)
+    double* Ustar;  // [2][KS] BR1 interface values
+    double* Fvt;    // [4][KN] contravariant viscous fluxes Ft2, Ft3, Gt2, Gt3
+    double* Fvtr;   // [4][KS] physical viscous fluxes at side nodes F2, F3, G2, G3
+    double* Fvout;  // [2][KS] outward viscous interface flux
+    double* eps;    // [K]
+    double* Kreg;   // [3][KN] 2N-storage register
+    double* Wn;     // [3][KN] state at the start of a step
+    double* R;      // [3][KN] right-hand side of the current stage
+    double* part;   // reduction partials
+    double* dt;     // [4]: dt in use, dt_cfl, dt_pos
+    unsigned long long* dtbits;  // [2]: max of lambda/J, max of inverse positivity dt
+    int* status;    // [1] status bits
+};
+
+}  // namespace swe
+
+struct swe_ctx {
+    int device = 0;
+    swe_params p{};
+    double sigma_min = 0, sigma_max = 0, h_tol = 1e-4;
+    swe::DeviceMesh m{};
+    swe::Work w{};
+    std::vector<void*> allocations;
+    int64_t launches = 0;
+    // timing
+    bool timing = false;
+    std::vector<cudaEvent_t> ev;
+    std::vector<int> ev_class;
+    int ev_used = 0;
+};
+
+namespace swe {
+
+// Kernel launchers (one translation unit per family).
+void init_tables_volume();
+void init_tables_face();
+void init_tables_av();
+
+void launch_prim(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
+void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop);
+// mode 0: limiter only; 1: 2N-storage stage K = a K + dt R, W += b K;
+// 2: SSP stage W = a Wn + b (W + dt R)
+void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,
+                   const double* dt_dev, cudaStream_t s, const int* stop);
+void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, const int* stop);
+void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
+                 const int* stop);
+void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cudaStream_t s);
+
+// Timing bracket of one launch.
+struct Timed {
+    swe_ctx* c;
+    cudaStream_t s;
+    int idx = -1;
+    Timed(swe_ctx* c, int cls, cudaStream_t s);
+    ~Timed();
+};
+
+}  // namespace swe

@@ -1,0 +1,191 @@
+"""Python binding of the swedg C ABI (include/swedg.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library. PyTorch provides device memory and streams. There is no CPU
+fallback; if the library cannot be built or loaded, or no CUDA device is
+present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+import os
+
+import numpy as np
+
+from . import build as _build
+
+OK, ERR_ARG, ERR_GEOM, ERR_NEG_MEAN, ERR_NONFINITE, ERR_CUDA = 0, -1, -2, -3, -4, -5
+KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "update": 5, "dt": 6,
+                  "reduce": 7}
+
+SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
+           "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_read",
+           "swe_launches", "swe_info", "swe_last_error"]
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("flux", ctypes.c_int), ("av", ctypes.c_int), ("eps0", ctypes.c_double),
+                ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
+                ("limiter", ctypes.c_int), ("h_tol", ctypes.c_double), ("rk", ctypes.c_int),
+                ("cfl", ctypes.c_double)]
+
+
+class SweError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"swedg error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def lib():
+    """Load (building first if needed) libswedg.so and declare its C ABI."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = _build.build()
+    L = ctypes.CDLL(path)
+    vp, dp, i32p = ctypes.c_void_p, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)
+    L.swe_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, i32p, i32p, i32p, dp, ctypes.c_double,
+                             ctypes.POINTER(Params), ctypes.POINTER(vp)]
+    L.swe_destroy.argtypes = [vp]
+    L.swe_destroy.restype = None
+    L.swe_rhs.argtypes = [vp, vp, vp, vp]
+    L.swe_limit.argtypes = [vp, vp, vp]
+    L.swe_max_dt.argtypes = [vp, vp, dp, dp, vp]
+    L.swe_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, dp, vp]
+    L.swe_mass.argtypes = [vp, vp, dp, vp]
+    L.swe_entropy.argtypes = [vp, vp, dp, vp]
+    L.swe_get_epsilon.argtypes = [vp, vp, vp]
+    L.swe_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
+    L.swe_timing.argtypes = [vp, ctypes.c_int]
+    L.swe_timing_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64)]
+    L.swe_launches.argtypes = [vp]
+    L.swe_launches.restype = ctypes.c_int64
+    L.swe_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
+                           ctypes.POINTER(ctypes.c_int)]
+    L.swe_last_error.argtypes = []
+    L.swe_last_error.restype = ctypes.c_char_p
+    _lib = L
+    return L
+
+
+def _check(rc):
+    if rc != OK:
+        raise SweError(rc, lib().swe_last_error().decode())
+    return rc
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+class SweContext:
+    """One mesh + parameter set on the current CUDA device (swe_create)."""
+
+    def __init__(self, N, K, x, y, EToE, EToF, flip, b, g=9.81, flux=1, av=False, eps0=0.0,
+                 sigma_min=math.nan, sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("swedg needs a CUDA device; there is no CPU path")
+        L = lib()
+        self.N, self.K, self.n = int(N), int(K), int(N) + 1
+        self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
+                             int(limiter), float(h_tol), int(rk), float(cfl))
+        arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, b)]
+        cons = [np.ascontiguousarray(a, dtype=np.int32) for a in (EToE, EToF, flip)]
+        d = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        i = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        h = ctypes.c_void_p()
+        _check(L.swe_create(self.N, self.K, d(arrs[0]), d(arrs[1]), i(cons[0]), i(cons[1]), i(cons[2]),
+                            d(arrs[2]), float(g), ctypes.byref(self.params), ctypes.byref(h)))
+        self._h = h
+
+    @classmethod
+    def from_problem(cls, prob, **kw):
+        return cls(prob.N, prob.K, prob.x, prob.y, prob.EToE, prob.EToF, prob.flip, prob.b, prob.g, **kw)
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value and _lib is not None:
+            _lib.swe_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _state(self, W):
+        import torch
+        if not (isinstance(W, torch.Tensor) and W.is_cuda and W.dtype == torch.float64 and W.is_contiguous()):
+            raise ValueError("state must be a contiguous float64 CUDA tensor")
+        if tuple(W.shape) != (3, self.K, self.n, self.n):
+            raise ValueError(f"state shape {tuple(W.shape)} != {(3, self.K, self.n, self.n)}")
+        return ctypes.c_void_p(W.data_ptr())
+
+    def rhs(self, W, R=None, stream=None):
+        import torch
+        if R is None:
+            R = torch.empty_like(W)
+        _check(lib().swe_rhs(self._h, self._state(W), self._state(R), _stream(stream)))
+        return R
+
+    def limit(self, W, stream=None):
+        _check(lib().swe_limit(self._h, self._state(W), _stream(stream)))
+        return W
+
+    def max_dt(self, W, stream=None):
+        dc, dp = ctypes.c_double(), ctypes.c_double()
+        _check(lib().swe_max_dt(self._h, self._state(W), ctypes.byref(dc), ctypes.byref(dp), _stream(stream)))
+        return dc.value, dp.value
+
+    def step(self, W, dt=0.0, nsteps=1, stream=None, raise_on_error=True):
+        dl = ctypes.c_double(0.0)
+        rc = lib().swe_step(self._h, self._state(W), float(dt), int(nsteps), ctypes.byref(dl), _stream(stream))
+        if raise_on_error:
+            _check(rc)
+        return rc, dl.value
+
+    def mass(self, W, stream=None):
+        out = (ctypes.c_double * 3)()
+        _check(lib().swe_mass(self._h, self._state(W), out, _stream(stream)))
+        return np.array(out[:])
+
+    def entropy(self, W, stream=None):
+        e = ctypes.c_double()
+        _check(lib().swe_entropy(self._h, self._state(W), ctypes.byref(e), _stream(stream)))
+        return e.value
+
+    def epsilon(self, stream=None):
+        import torch
+        eps = torch.empty(self.K, dtype=torch.float64, device="cuda")
+        _check(lib().swe_get_epsilon(self._h, ctypes.c_void_p(eps.data_ptr()), _stream(stream)))
+        return eps
+
+    def status(self, stream=None):
+        b = ctypes.c_int()
+        _check(lib().swe_status(self._h, ctypes.byref(b), _stream(stream)))
+        return b.value
+
+    def timing(self, on=True):
+        _check(lib().swe_timing(self._h, int(on)))
+
+    def timing_read(self, which):
+        ms, cnt = ctypes.c_double(), ctypes.c_int64()
+        w = KERNEL_CLASSES[which] if isinstance(which, str) else int(which)
+        _check(lib().swe_timing_read(self._h, w, ctypes.byref(ms), ctypes.byref(cnt)))
+        return ms.value, cnt.value
+
+    def launches(self):
+        return int(lib().swe_launches(self._h))
+
+    def info(self):
+        N, K, nf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        _check(lib().swe_info(self._h, ctypes.byref(N), ctypes.byref(K), ctypes.byref(nf)))
+        return N.value, K.value, nf.value
