@@ -1,0 +1,347 @@
+#!/usr/bin/env python3
+"""Benchmark of the entropy-stable DGSEM shallow-water hot path on GB300.
+
+One step = one five-stage LSRK4(5) time step of the whole path on the
+degree-sweep dam-break workload (N=7, 256x256 curved periodic quads, 4.19M
+LGL nodes, FP64): per stage the primitives, the entropy-stable interface
+flux, the artificial-viscosity indicator and BR1 gradients, the viscous
+interface average, the volume kernel (flux differencing, source, lifts,
+viscous divergence, 1/J) and the stage update with the positivity limiter;
+per step the device-side CFL/positivity time step, and the mass and entropy
+integrals read back to the host. Each step starts from the same input state
+(one batch). The metric is RHS node-updates per second: 5 right-hand sides x
+K (N+1)^2 nodes per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun with N > 1 every rank runs an independent replica on its own
+GPU (the method needs no cross-GPU exchange for independent problems), the
+time is the maximum over ranks and the value the sum of the ranks' work.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+RK_STAGES = 5
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=7)
+    ap.add_argument("--K1", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def workload_config(N, K1):
+    return {"workload": f"dam_break N={N} {K1}x{K1} curved periodic quads, ES flux + AV + limiter, LSRK4(5)",
+            "N": N, "K": K1 * K1, "nodes": K1 * K1 * (N + 1) ** 2, "eps0": 0.025, "cfl": 0.5,
+            "rk": "LSRK4(5)", "l2": "inputs larger than L2 (state 0.1 GB + geometry 0.4 GB per step)"}
+
+
+# ---------------------------------------------------------------------------
+# Clock sampling during the timed region
+# ---------------------------------------------------------------------------
+
+class Clocks:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index, enabled=True):
+        self.index, self.p, self.out = index, None, None
+        if not enabled:
+            return
+        try:
+            self.out = open(os.devnull, "w")
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={index}", f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return None
+        self.p.terminate()
+        try:
+            txt, _ = self.p.communicate(timeout=5)
+        except Exception:
+            self.p.kill()
+            txt = ""
+        rows = [r.split(",") for r in txt.strip().splitlines() if r.count(",") >= 8]
+        if not rows:
+            return None
+        sm = sorted(float(r[1]) for r in rows)
+        mx = max(float(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[j] for r in rows for j in range(4) if r[5 + j].strip().lower() == "active"})
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": mx, "reasons": reasons, "samples": len(rows),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].strip() not in ("", "[N/A]"))}
+
+
+# ---------------------------------------------------------------------------
+# Algorithmic work of the volume kernel (flux differencing + per-node terms,
+# entropy-stable path; the viscous divergence of the few viscous elements is
+# not counted, so the figure is a lower bound)
+# ---------------------------------------------------------------------------
+
+def volume_flops_per_node(N):
+    """28 flops per symmetric pair (2 metric sums, 4 state sums, Q: 3,
+    P: 1, X2: 3, X3: 3, two-sided accumulation of 3 components: 12), N pairs
+    per node (N(N+1)/2 per line, 2(N+1) lines per element); per node 9 flops
+    (2gh, the three rescalings and the two source products) and the interface
+    lift, 3 fused multiply-adds on each of the 4(N+1) side nodes."""
+    n = N + 1
+    return 28 * N + 9 + 6 * 4 * n / (n * n)
+
+
+def volume_bytes_per_node(N):
+    """Compulsory DRAM bytes: W (24), velocities (16), contravariant metric
+    vectors (32), 1/J (8), source coefficients (16), R (24), interface flux
+    traces 3 x 4(N+1) doubles per element."""
+    n = N + 1
+    return 120 + 3 * 8 * 4 * n / (n * n)
+
+
+def volume_traffic(N, nodes):
+    """DRAM bytes per launch of the volume kernel from the committed ncu
+    summary (dram__bytes_read.sum + dram__bytes_write.sum per node, measured
+    on a smaller case of the same kernel and scaled by the node count), or
+    None when the kernel source changed since the counters were taken."""
+    import hashlib
+    src = os.path.join(ROOT, "paper_1804_02221_gb300", "csrc", "k_volume.cu")
+    summ = os.path.join(ROOT, "profiles", "volume_kernel_dam_break_N7.txt")
+    if not os.path.exists(summ):
+        return None
+    sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+    vals = {}
+    for line in open(summ):
+        if "=" in line and line.strip().startswith("traffic."):
+            k, v = line.strip().split("=", 1)
+            vals[k.strip()] = v.strip()
+    if vals.get("traffic.kernel_sha256_16") != sha or int(vals.get("traffic.N", -1)) != N:
+        return None
+    return float(vals["traffic.dram_bytes_per_node"]) * nodes
+
+
+def fp64_peak_gflops(sm_mhz):
+    """152 SMs x 2 FP64 fused multiply-adds per clock (measured: 1.9 DFMA/clk/SM
+    with independent chains at 2070 MHz nominal) x 2 flops."""
+    return 152 * 2 * 2 * sm_mhz * 1e6 / 1e9
+
+
+# ---------------------------------------------------------------------------
+# Oracle timing (CPU baseline and reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_rate(N, K1, steps, warmup=0):
+    from oracle import oracle as O
+    from paper_1804_02221_gb300 import inputs as I
+    p = I.dam_break(N=N, K1=K1)
+    o = O.Oracle(p, flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    for _ in range(warmup):
+        o.step(p.W, 0.0, 1)
+        o.entropy(p.W)
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        W, rc, _ = o.step(p.W, 0.0, 1)
+        o.entropy(W)
+        o.mass(W)
+    t = (time.perf_counter() - t0) / max(steps, 1)
+    return RK_STAGES * p.nodes / t, t, O.threads(), p.nodes
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    N = args.N
+    K1 = 64  # bounded sample: same degree and recipe on 64x64 quads (262k nodes)
+    rate, t, cores, nodes = oracle_rate(N, K1, args.steps, args.warmup)
+    sample = f"dam_break N={N} on {K1}x{K1} quads ({nodes} nodes), {args.steps} full LSRK4(5) steps"
+    line = {"impl": "reference", "metric": "RHS node-updates/s (FP64)", "value": rate,
+            "unit": "node-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": workload_config(N, 2048 // (N + 1) if args.K1 is None else args.K1),
+            "cpu_baseline": {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": rate, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    import numpy as np
+    import torch
+
+    from paper_1804_02221_gb300 import inputs as I
+    from paper_1804_02221_gb300 import swedg
+
+    ws, rank, local = dist_env()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    N = args.N
+    K1 = args.K1 or int(round(2048 / (N + 1)))
+    prob = I.dam_break(N=N, K1=K1)
+    kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    ctx = swedg.SweContext.from_problem(prob, **kw)
+    W0 = torch.from_numpy(prob.W).cuda()
+    W = torch.empty_like(W0)
+    nodes = prob.nodes
+    stream = torch.cuda.current_stream()
+
+    def one_step(Wd):
+        ctx.step(Wd, 0.0, 1)
+        ctx.entropy(Wd)
+        ctx.mass(Wd)
+
+    for _ in range(args.warmup):
+        W.copy_(W0)
+        one_step(W)
+    torch.cuda.synchronize()
+
+    # ---- device-resident timed region ----
+    clocks = Clocks(local, enabled=not args.no_clocks)
+    time.sleep(0.3)
+    ctx.timing(True)
+    l0 = ctx.launches()
+    barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        W.copy_(W0)
+        one_step(W)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    launches = ctx.launches() - l0
+    clk = clocks.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    vol_ms, vol_n = ctx.timing_read("volume")
+    kernels = {}
+    for name in swedg.KERNEL_CLASSES:
+        t, c = ctx.timing_read(name)
+        if c:
+            kernels[name] = {"ms_total": t, "launches": c, "ms_per_launch": t / c}
+    ctx.timing(False)
+
+    # ---- end to end through the C ABI with host buffers ----
+    Wh = torch.from_numpy(prob.W).pin_memory()
+    for _ in range(2):
+        W.copy_(Wh, non_blocking=True)
+        one_step(W)
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        W.copy_(Wh, non_blocking=True)
+        one_step(W)  # the diagnostics are read back to the host
+    torch.cuda.synchronize()
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+
+    # ---- RHS alone: entropy-conservative vs entropy-stable + AV ----
+    rhs_rates = {}
+    R = torch.empty_like(W0)
+    for name, kk in (("ES+AV", kw), ("EC", dict(flux=0))):
+        c2 = ctx if name == "ES+AV" else swedg.SweContext.from_problem(prob, **kk)
+        for _ in range(3):
+            c2.rhs(W0, R)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(10):
+            c2.rhs(W0, R)
+        b.record(stream)
+        torch.cuda.synchronize()
+        rhs_rates[name] = nodes / (a.elapsed_time(b) / 10 * 1e-3)
+
+    # ---- reduce over ranks ----
+    t_step = ms
+    if dist is not None:
+        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_step, e2e_ms = float(tt[0]), float(tt[1])
+    value = ws * RK_STAGES * nodes / (t_step * 1e-3)
+    e2e_value = ws * RK_STAGES * nodes / (e2e_ms * 1e-3)
+
+    if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
+        return
+
+    sm_mhz = clk["sm_mhz"] if clk else 2070.0
+    vol_avg_ms = vol_ms / vol_n if vol_n else float("nan")
+    flops = volume_flops_per_node(N) * nodes
+    achieved = flops / (vol_avg_ms * 1e-3) / 1e12
+    peak = fp64_peak_gflops(sm_mhz) / 1e3
+    traffic = volume_traffic(N, nodes)
+    line = {
+        "metric": "RHS node-updates/s (FP64)", "value": value, "unit": "node-updates/s",
+        "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": workload_config(N, K1),
+        "roofline": {"bound": "alu", "kernel": "volume", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                     "ms_per_launch": vol_avg_ms, "flops_per_launch": flops,
+                     "bytes_per_launch": volume_bytes_per_node(N) * nodes,
+                     "peak_note": "FP64 ALU: 152 SMs x 2 DFMA/clk x 2 flops at the median SM clock sampled "
+                                  "during the timed region (MEASURED_PEAKS has no FP64 figure)"},
+        "e2e": {"value": e2e_value, "unit": "node-updates/s", "h2d_bytes_per_step": int(W0.numel() * 8),
+                "d2h_bytes_per_step": 4 * 8},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "kernels": kernels,
+        "rhs_only_node_updates_per_s": rhs_rates,
+        "scalar_updates_per_s": 3 * value,
+    }
+    if not args.no_cpu_baseline and ws == 1:
+        rate, t, cores, n_s = oracle_rate(N, K1, 1)
+        line["cpu_baseline"] = {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
+                                "sample": f"one LSRK4(5) step of the same workload ({n_s} nodes), "
+                                          f"{t:.1f} s on {cores} OpenMP threads"}
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()
