@@ -147,6 +147,33 @@ int64_t swe_launches(const swe_ctx* ctx);
 /* Sizes of a context: N, K and the number of unique faces. */
 int swe_info(const swe_ctx* ctx, int* N, int* K, int* nfaces);
 
+/* Allocation-free diagnostic integrals, for callers that cannot call
+ * cudaMalloc (the paper has no counterpart: this is an interface for
+ * embedding). Such callers include code running while a host framework's
+ * caching allocator owns the device memory pool, real-time loops that cannot
+ * afford the device synchronisation implied by cudaMalloc/cudaFree, and hosts
+ * with a memory budget fixed at start-up. The call computes the same sums as
+ * swe_mass and swe_entropy without a context:
+ *   out4[0..2] = sum_k sum_ij wJ W_c,  out4[3] = sum_k sum_ij wJ e(W)
+ * (e of Eq. entropyFunction), with
+ *   W    device, 3*K*(N+1)^2 doubles, the state planes (h, hu, hv);
+ *   wJ   device, K*(N+1)^2 doubles, w_i w_j J at every node;
+ *   b    device, K*(N+1)^2 doubles, the bathymetry;
+ *   out4 device, 4 doubles, written asynchronously on `stream`.
+ * It allocates nothing: the per-element partial sums live in one fixed
+ * device array of 4*SWE_NOALLOC_MAX_ELEMENTS doubles (2 MiB), which every GPU
+ * that loads the library holds until the process exits. K above
+ * SWE_NOALLOC_MAX_ELEMENTS is rejected with SWE_ERR_ARG. The first call on
+ * each device resolves that array's device address (cudaGetSymbolAddress,
+ * with the device current), so make the first call on a device before any
+ * stream capture. Every call writes each partial it later reads, so nothing
+ * needs clearing, but all calls share the one array: calls that may overlap
+ * on the GPU (different streams, or different host threads) race and must be
+ * serialised by the caller. */
+#define SWE_NOALLOC_MAX_ELEMENTS 65536
+int swe_integrals_noalloc(int N, int K, const double* W, const double* wJ, const double* b, double g,
+                          double* out4, void* stream);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* swe_last_error(void);
 

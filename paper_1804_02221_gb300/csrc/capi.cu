@@ -85,6 +85,8 @@ void free_all(swe_ctx* c) {
 
 namespace swe {
 
+int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
+
 Timed::Timed(swe_ctx* c_, int cls, cudaStream_t s_) : c(c_), s(s_) {
     c->launches++;
     if (c->timing && c->ev_used < (int)c->ev_class.size()) {

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <string>
 #include <vector>
 
 #include "../../include/swedg.h"
@@ -147,6 +148,9 @@ void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, con
 void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
                  const int* stop);
 void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cudaStream_t s);
+
+// Record the text of an error for swe_last_error() and return code.
+int set_last_error(int code, const std::string& msg);
 
 // Timing bracket of one launch.
 struct Timed {

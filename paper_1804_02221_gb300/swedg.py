@@ -21,7 +21,7 @@ KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "u
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_read",
-           "swe_launches", "swe_info", "swe_last_error"]
+           "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc"]
 
 
 class Params(ctypes.Structure):
@@ -70,6 +70,7 @@ def lib():
     L.swe_launches.restype = ctypes.c_int64
     L.swe_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)]
+    L.swe_integrals_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp]
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -86,6 +87,23 @@ def _stream(stream):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return ctypes.c_void_p(s.cuda_stream)
+
+
+def integrals_noalloc(N, W, wJ, b, g, out4=None, stream=None):
+    """swe_integrals_noalloc: mass, momenta and entropy of device state W
+    without a context and without any allocation by the library (the output
+    tensor out4 is allocated here unless the caller passes one)."""
+    import torch
+    K = W.shape[1]
+    if out4 is None:
+        out4 = torch.empty(4, dtype=torch.float64, device=W.device)
+    for a in (W, wJ, b, out4):
+        if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
+            raise ValueError("swe_integrals_noalloc needs contiguous float64 CUDA tensors")
+    _check(lib().swe_integrals_noalloc(int(N), int(K), ctypes.c_void_p(W.data_ptr()),
+                                       ctypes.c_void_p(wJ.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                       float(g), ctypes.c_void_p(out4.data_ptr()), _stream(stream)))
+    return out4
 
 
 class SweContext:
