@@ -120,6 +120,7 @@ extern "C" int swe_create(int N, int K, const double* x, const double* y, const 
     if (p->flux != 0 && p->flux != 1) return fail(SWE_ERR_ARG, "swe_create: flux must be 0 or 1");
     if (p->rk != 0 && p->rk != 1) return fail(SWE_ERR_ARG, "swe_create: rk must be 0 or 1");
     if (p->av && !(p->eps0 >= 0.0)) return fail(SWE_ERR_ARG, "swe_create: eps0 must be >= 0");
+    if (!isnan(p->h_tol) && !(p->h_tol >= 0.0)) return fail(SWE_ERR_ARG, "swe_create: h_tol must be >= 0");
     const int n = N + 1, nn = n * n;
     const long long KN = (long long)K * nn, KS = (long long)K * 4 * n;
     if (KN * 3 > 2147483647LL) return fail(SWE_ERR_ARG, "swe_create: mesh too large for 32-bit node ids");
@@ -200,6 +201,35 @@ extern "C" int swe_create(int N, int K, const double* x, const double* y, const 
             }
     }
 
+    // ---- pair constants of the volume kernel ----
+    // For line l in direction d (0: xi-line j = l, 1: eta-line i = l) and the
+    // pair (i, q), i < q, of positions along it: the contravariant vector a of
+    // the direction summed over the two nodes, times w_i w_j D_iq / 4 with
+    // (w_i w_j) the quadrature weight of the pair's first node. The volume
+    // kernel accumulates w_i w_j L with these, so that the partner node takes
+    // the negative (w_q D_qi = -w_i D_iq, the SBP property).
+    const int NP = N * (N + 1) / 2;
+    std::vector<double> pm((size_t)K * 2 * NP * 2 * n), fwJ(KN);
+    for (long long a = 0; a < KN; ++a) fwJ[a] = -1.0 / wJ[a];
+    for (int k = 0; k < K; ++k)
+        for (int d = 0; d < 2; ++d) {
+            const double* vx = d == 0 ? axx.data() : aex.data();
+            const double* vy = d == 0 ? axy.data() : aey.data();
+            for (int l = 0; l < n; ++l) {
+                int pr = 0;
+                for (int i = 0; i < n; ++i)
+                    for (int q = i + 1; q < n; ++q, ++pr) {
+                        const long long na = (long long)k * nn + (d == 0 ? l * n + i : i * n + l);
+                        const long long nb = (long long)k * nn + (d == 0 ? l * n + q : q * n + l);
+                        const int ii = d == 0 ? i : l, jj = d == 0 ? l : i;
+                        const double s = w[ii] * w[jj] * D[i * n + q] * 0.25;
+                        const size_t base = ((((size_t)k * 2 + d) * NP + pr) * 2) * n + l;
+                        pm[base] = s * (vx[na] + vx[nb]);
+                        pm[base + n] = s * (vy[na] + vy[nb]);
+                    }
+            }
+        }
+
     // ---- unique faces and element sides ----
     std::vector<int32_t> f_im, f_ip, f_tm, f_tp, s_nb(KS);
     std::vector<double> f_nx, f_ny, f_js, f_bm, f_bp, s_nx(KS), s_ny(KS), s_rwa(KS);
@@ -250,9 +280,10 @@ extern "C" int swe_create(int N, int K, const double* x, const double* y, const 
     // ---- device ----
     swe_ctx* c = new swe_ctx();
     cudaError_t err = cudaGetDevice(&c->device);
+    if (err == cudaSuccess) err = cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device);
     if (err != cudaSuccess) {
         delete c;
-        return cuda_fail(err, "swe_create: cudaGetDevice");
+        return cuda_fail(err, "swe_create: device query");
     }
     init_device_tables(c->device);
     c->p = *p;
@@ -274,6 +305,7 @@ extern "C" int swe_create(int N, int K, const double* x, const double* y, const 
     if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: upload"); }
     UP(m.axx, axx) UP(m.axy, axy) UP(m.aex, aex) UP(m.aey, aey) UP(m.rJ, rJ) UP(m.wJ, wJ)
     UP(m.srcx, srcx) UP(m.srcy, srcy) UP(m.bn, bn) UP(m.nax, cfln) UP(m.rvol, rvol)
+    UP(m.fwJ, fwJ) UP(m.pm, pm)
     UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
     UP(m.f_ny, f_ny) UP(m.f_js, f_js) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
     UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
@@ -322,11 +354,14 @@ extern "C" void swe_destroy(swe_ctx* c) {
 
 namespace {
 
-void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done) {
+// prim_done: the velocities of W are in the work buffer (written by the
+// previous stage update); eps_done: so are its element viscosities.
+void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done,
+               bool eps_done = false) {
     if (!prim_done) swe::launch_prim(c, W, s, stop);
     swe::launch_surface(c, W, s, stop);
     if (c->p.av) {
-        swe::launch_av(c, W, s, stop);
+        swe::launch_av(c, W, s, stop, eps_done);
         swe::launch_visc_face(c, s, stop);
     }
     swe::launch_volume(c, W, R, s, stop);
@@ -350,7 +385,7 @@ extern "C" int swe_limit(swe_ctx* c, double* W, void* stream) {
     if (!c || !W) return fail(SWE_ERR_ARG, "swe_limit: NULL argument");
     swe_params saved = c->p;
     c->p.limiter = 1;
-    swe::launch_update(c, 0, W, 0.0, 0.0, 0.0, nullptr, (cudaStream_t)stream, nullptr);
+    swe::launch_update(c, 0, W, 0.0, 0.0, 0.0, nullptr, (cudaStream_t)stream, nullptr, false);
     c->p = saved;
     return check_launch("swe_limit");
 }
@@ -378,25 +413,24 @@ extern "C" int swe_step(swe_ctx* c, double* W, double dt, int nsteps, double* dt
     const bool adaptive = !(dt > 0.0);
     const double* dtd = adaptive ? c->w.dt : nullptr;
     cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+    // Every stage update also writes the velocities of its new state, so only
+    // the first stage of the call needs the primitives kernel.
+    bool uv_valid = false;
     for (int st = 0; st < nsteps; ++st) {
         swe::launch_copy(c, W, c->w.Wn, n3, s, stop);
-        bool prim_done = false;
-        if (adaptive) {
+        if (!uv_valid) {
             swe::launch_prim(c, W, s, stop);
-            swe::launch_dt(c, W, 0.0, s, stop);
-            prim_done = true;
+            uv_valid = true;
         }
-        if (c->p.rk == 0) {
-            for (int stage = 0; stage < 5; ++stage) {
-                rhs_chain(c, W, c->w.R, s, stop, prim_done && stage == 0);
-                swe::launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop);
-            }
-        } else {
-            const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
-            for (int stage = 0; stage < 3; ++stage) {
-                rhs_chain(c, W, c->w.R, s, stop, prim_done && stage == 0);
-                swe::launch_update(c, 2, W, ca[stage], cb[stage], dt, dtd, s, stop);
-            }
+        if (adaptive) swe::launch_dt(c, W, 0.0, s, stop);
+        const int stages = c->p.rk == 0 ? 5 : 3;
+        const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+        for (int stage = 0; stage < stages; ++stage) {
+            rhs_chain(c, W, c->w.R, s, stop, true);
+            if (c->p.rk == 0)
+                swe::launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop, true);
+            else
+                swe::launch_update(c, 2, W, ca[stage], cb[stage], dt, dtd, s, stop, true);
         }
     }
     int rc = check_launch("swe_step");

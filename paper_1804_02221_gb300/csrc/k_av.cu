@@ -1,10 +1,29 @@
-// Artificial viscosity, per element: the modal smoothness indicator and the
-// viscosity epsilon_k (App. A), then, only where epsilon_k > 0, the BR1
-// gradients of u and v (Eq. BR1, strong form with the (U* - u) lift on the
-// outward normal) and the viscous fluxes F^v = h eps (U1, V1),
-// G^v = h eps (U2, V2) (Thm. 1) with their contravariant forms for the volume
-// kernel and their values at the element's side nodes for the interface
-// average.
+// Artificial viscosity: the element smoothness indicator and viscosity
+// epsilon_k (App. A), then, only where epsilon_k > 0, the BR1 gradients of u
+// and v (Eq. BR1, strong form with the (U* - u) lift on the outward normal)
+// and the viscous fluxes F^v = h eps (U1, V1), G^v = h eps (U2, V2)
+// (Thm. 1), with their contravariant forms for the volume kernel and their
+// values at the element's side nodes for the interface average.
+//
+// Indicator without the full modal transform. With Qhat = Vinv Q Vinv^T the
+// three energies of Eq. sigmadof are
+//   E_all = sum Qhat^2,  E_top = sum over modes of degree N in some direction,
+//   E_sub = sum over modes of degree N-1 in some direction and <= N-1 in both.
+// LGL quadrature (N+1 nodes) integrates f^2 of a degree-N polynomial f up to
+// one term: int f^2 = sum_i w_i f_i^2 - k f_N^2, k = (N+1)/N, f_N its top
+// normalised Legendre coefficient (the rule is exact to degree 2N-1, and its
+// error on degree 2N depends only on the leading coefficient). Applied along
+// each direction, with the projections
+//   y_xi[j] = sum_i Vinv[N][i] Q[i][j],   y_eta[i] = sum_j Vinv[N][j] Q[i][j],
+//   z_xi[j] = sum_i Vinv[N-1][i] Q[i][j], z_eta[i] = sum_j Vinv[N-1][j] Q[i][j],
+//   B0 = Qhat[N][N], C0 = Qhat[N][N-1], B2 = Qhat[N-1][N], C2 = Qhat[N-1][N-1],
+// and S_y = sum w y^2 etc.:
+//   E_all = sum_ij w_i w_j Q_ij^2 - k (S_yxi + S_yeta) + k^2 B0^2
+//   E_top = S_yxi + S_yeta - (2k+1) B0^2
+//   E_sub = S_zxi - (k+1) B2^2 + S_zeta - (k+1) C0^2 - C2^2
+// which costs O(N^2) per element instead of the O(N^3) transform. One warp
+// evaluates 8 elements at a time, so the per-element reductions are short
+// four-lane butterflies and the scalar work runs on 8 lanes at once.
 #include <math.h>
 
 #include "kcommon.cuh"
@@ -20,182 +39,237 @@ struct AvArgs {
     double* Fvt;
     double* Fvtr;
     double* eps;
-    double eps0, smin, smax;
+    EpsParams ep;
     const int* stop;
 };
 
+constexpr int AV_EPW = 8;  // elements per warp
+constexpr int AV_WPB = 2;  // warps per block
+
+// epsilon from the nine sums of one element (S_yxi, S_yeta, S_zxi, S_zeta,
+// B0, C0, B2, C2, sum w w Q^2).
 template <int N>
-constexpr int av_ne() {
-    return (128 / ((N + 1) * (N + 1))) > 0 ? 128 / ((N + 1) * (N + 1)) : 1;
+__device__ __forceinline__ double epsilon_from_sums(const double* S, const EpsParams& ep) {
+    constexpr double k1 = (N + 1.0) / N;
+    const double B0 = S[4], C0 = S[5], B2 = S[6], C2 = S[7];
+    const double e_all = S[8] - k1 * (S[0] + S[1]) + k1 * k1 * B0 * B0;
+    const double e_top = S[0] + S[1] - (2.0 * k1 + 1.0) * B0 * B0;
+    const double e_sub = S[2] - (k1 + 1.0) * B2 * B2 + S[3] - (k1 + 1.0) * C0 * C0 - C2 * C2;
+    const double den2 = e_all - e_top;
+    // both ratios at most 10^sigma_min (epsilon = 0, the common case for
+    // smooth elements) is decided without a division
+    const bool flat = !(e_top > ep.rmin * e_all) && (N < 2 || !(e_sub > ep.rmin * den2));
+    if (flat || ep.eps0 == 0.0) return 0.0;
+    double r = e_all > 0.0 ? e_top / e_all : 0.0;
+    if (N >= 2 && den2 > 0.0) r = fmax(r, e_sub / den2);
+    if (!(r > ep.rmin)) return 0.0;
+    if (r >= ep.rmax) return ep.eps0;
+    // epsilon is continuous in sigma = log10(r), so the comparisons with
+    // 10^sigma_min and 10^sigma_max above decide the two flat branches
+    const double sig = log10(r);
+    if (sig >= ep.smax) return ep.eps0;
+    if (!(sig > ep.smin)) return 0.0;
+    return 0.5 * ep.eps0 *
+           (1.0 + sin(3.14159265358979323846 * (sig - 0.5 * (ep.smax + ep.smin)) / (ep.smax - ep.smin)));
 }
 
-template <int N>
-__global__ void k_av(AvArgs a) {
-    constexpr int n = N + 1, nn = n * n, NE = av_ne<N>(), BLK = NE * nn;
+// EPS_GIVEN: epsilon of this state is already in the work buffer; only the
+// viscous fluxes remain.
+template <int N, bool EPS_GIVEN>
+__global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
+    constexpr int n = N + 1, nn = n * n, P4 = 4 * n, PER = (nn + 31) / 32;
     constexpr double iw0 = N * (N + 1) / 2.0;
-    __shared__ double sh_h[BLK], sh_u[BLK], sh_v[BLK], sh_T[BLK];
-    __shared__ double sh_q[4][BLK];
-    __shared__ double sh_D[nn], sh_Vi[nn];
-    __shared__ double sh_eps[NE];
+    __shared__ double sD[nn], sVi[nn], sWW[nn];
+    __shared__ double sQ[AV_WPB][AV_EPW][nn];
+    __shared__ double sP[AV_WPB][AV_EPW][P4];
+    __shared__ double sS[AV_WPB][AV_EPW][9];
+    __shared__ double sUV[AV_WPB][2][nn];
+    __shared__ double sEps[AV_WPB][AV_EPW];
     if (stopped(a.stop)) return;
     const DeviceMesh& m = a.m;
-    const int t = threadIdx.x;
-    const int e = t / nn, node = t - e * nn;
-    const long long k = (long long)blockIdx.x * NE + e;
-    const bool valid = t < BLK && k < m.K;
-    const long long gid = k * nn + node;
-    if (t < nn) {
-        sh_D[t] = Dm<N>(t / n, t % n);
-        sh_Vi[t] = c_Vinv[mat_offset(N) + t];
-    }
-    if (t < BLK) {
-        sh_h[t] = valid ? a.W[gid] : 0.0;
-        sh_u[t] = valid ? a.uv[gid] : 0.0;
-        sh_v[t] = valid ? a.uv[m.KN + gid] : 0.0;
-    }
-    __syncthreads();
-    const int i = node % n, j = node / n;
-    const int eb = e * nn;
-    // modal coefficients Qhat = Vinv Q Vinv^T (Eq. TransformationToModal),
-    // Q[i][j] = h at (xi_i, eta_j): first T[a][j] = sum_i Vinv[a][i] Q[i][j]
-    if (t < BLK) {
-        double s = 0.0;
-        for (int q = 0; q < n; ++q) s = fma(sh_Vi[i * n + q], sh_h[eb + j * n + q], s);
-        sh_T[t] = s;  // T[a = i][j]
-    }
-    __syncthreads();
-    if (t < BLK) {
-        // Qhat[a = i][c = j] = sum_q T[a][q] Vinv[c][q]
-        double s = 0.0;
-        for (int q = 0; q < n; ++q) s = fma(sh_T[eb + q * n + i], sh_Vi[j * n + q], s);
-        const double q2 = s * s;
-        const bool top = (i == N) || (j == N);
-        const bool low = (i < N) && (j < N);
-        const bool sub = low && ((i == N - 1) || (j == N - 1));
-        sh_q[0][t] = q2;                 // all modes
-        sh_q[1][t] = top ? q2 : 0.0;     // a mode of degree N in some direction
-        sh_q[2][t] = low ? q2 : 0.0;     // degree <= N-1 in both
-        sh_q[3][t] = sub ? q2 : 0.0;     // degree N-1 in some direction, <= N-1 in both
-    }
-    __syncthreads();
-    // energy sums of Eq. sigmadof in a fixed order, then epsilon (App. A)
-    if (t < NE * 4) {
-        const int ee = t / 4, which = t - ee * 4;
-        double s = 0.0;
-        for (int q = 0; q < nn; ++q) s += sh_q[which][ee * nn + q];
-        sh_T[ee * nn + which] = s;  // T is free again
-    }
-    __syncthreads();
-    if (t < NE) {
-        const double den1 = sh_T[t * nn + 0], num1 = sh_T[t * nn + 1];
-        const double den2 = sh_T[t * nn + 2], num2 = sh_T[t * nn + 3];
-        double r = den1 > 0.0 ? num1 / den1 : 0.0;
-        if (N >= 2) {
-            const double r2 = den2 > 0.0 ? num2 / den2 : 0.0;
-            r = fmax(r, r2);
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) {
+        sD[t] = Dm<N>(t / n, t % n);
+        if (!EPS_GIVEN) {
+            sVi[t] = c_Vinv[mat_offset(N) + t];
+            sWW[t] = c_w[vec_offset(N) + t % n] * c_w[vec_offset(N) + t / n];
         }
-        double ep = 0.0;
-        if (a.eps0 != 0.0 && r > 0.0) {
-            const double sig = log10(r);
-            if (sig >= a.smax) ep = a.eps0;
-            else if (sig > a.smin)
-                ep = 0.5 * a.eps0 * (1.0 + sin(3.14159265358979323846 * (sig - 0.5 * (a.smax + a.smin)) /
-                                                (a.smax - a.smin)));
-        }
-        sh_eps[t] = ep;
-        if ((long long)blockIdx.x * NE + t < m.K) a.eps[(long long)blockIdx.x * NE + t] = ep;
     }
     __syncthreads();
-    if (!valid) return;
-    const double ep = sh_eps[e];
-    const bool bnd = (i == 0) || (i == N) || (j == 0) || (j == N);
-    const long long KS = m.KS;
-    auto side = [&](int f, int p) { return (k * 4 + f) * n + p; };
-    if (!(ep > 0.0)) {
-        if (bnd) {
-            auto zero = [&](int f, int p) {
-                const long long sl = side(f, p);
-                a.Fvtr[sl] = 0.0;
-                a.Fvtr[KS + sl] = 0.0;
-                a.Fvtr[2 * KS + sl] = 0.0;
-                a.Fvtr[3 * KS + sl] = 0.0;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const long long k0 = ((long long)blockIdx.x * AV_WPB + w) * AV_EPW;
+    if (k0 >= m.K) return;  // whole warps leave together; no block barrier follows
+    const int ne = (int)((m.K - k0) < AV_EPW ? (m.K - k0) : AV_EPW);
+    double(*Q)[nn] = sQ[w];
+
+    if (!EPS_GIVEN) {
+        // ---- water heights of the 8 elements (contiguous in memory) -------
+        for (int idx = lane; idx < AV_EPW * nn; idx += 32) {
+            const int e = idx / nn;
+            Q[e][idx - e * nn] = e < ne ? a.W[k0 * nn + idx] : 0.0;
+        }
+        __syncwarp();
+        // ---- the four projections of every element ------------------------
+        for (int s = lane; s < AV_EPW * P4; s += 32) {
+            const int e = s / P4, L = s - e * P4, t = L / n, p = L - t * n;
+            const double* vr = sVi + (t < 2 ? N : N - 1) * n;
+            double v = 0.0;
+            if ((t & 1) == 0) {
+#pragma unroll
+                for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][p * n + q], v);  // sum over i, j = p
+            } else {
+#pragma unroll
+                for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][q * n + p], v);  // sum over j, i = p
+            }
+            sP[w][e][L] = v;
+        }
+        // ---- sum w w Q^2: four lanes per element ---------------------------
+        const int e4 = lane >> 2, sub = lane & 3;
+        double swq = 0.0;
+        for (int node = sub; node < nn; node += 4) {
+            const double q = Q[e4][node];
+            swq = fma(sWW[node] * q, q, swq);
+        }
+        swq += __shfl_xor_sync(0xffffffffu, swq, 1);
+        swq += __shfl_xor_sync(0xffffffffu, swq, 2);
+        __syncwarp();
+        // ---- the eight projection sums: two per lane -----------------------
+        // sum index m: 0..3 weighted squares of y_xi, y_eta, z_xi, z_eta;
+        // 4: B0 = Vinv[N].y_xi, 5: C0 = Vinv[N-1].y_xi, 6: B2 = Vinv[N].z_xi,
+        // 7: C2 = Vinv[N-1].z_xi; each written as sum_p (c_p x_p) y_p
+#pragma unroll
+        for (int h2 = 0; h2 < 2; ++h2) {
+            const int mi = 2 * sub + h2;
+            const bool sq = mi < 4;
+            const double* x = sP[w][e4] + (sq ? mi : (mi < 6 ? 0 : 2)) * n;
+            const double* c = sVi + ((mi & 1) == 0 ? N : N - 1) * n;
+            double s = 0.0;
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                const double cp = sq ? c_w[vec_offset(N) + p] : c[p];
+                const double yp = sq ? x[p] : 1.0;
+                s = fma(cp * x[p], yp, s);
+            }
+            sS[w][e4][mi] = s;
+        }
+        if (sub == 0) sS[w][e4][8] = swq;
+        __syncwarp();
+        // ---- epsilon, one lane per element --------------------------------
+        if (lane < AV_EPW) {
+            const double ep = epsilon_from_sums<N>(sS[w][lane], a.ep);
+            sEps[w][lane] = ep;
+            if (lane < ne) a.eps[k0 + lane] = ep;
+        }
+    } else {
+        if (lane < AV_EPW) sEps[w][lane] = lane < ne ? a.eps[k0 + lane] : 0.0;
+    }
+    __syncwarp();
+
+    // ---- viscous fluxes of the viscous elements, zeros elsewhere -----------
+    const long long KS = m.KS, KN = m.KN;
+    for (int e = 0; e < ne; ++e) {
+        const double ep = sEps[w][e];
+        const long long k = k0 + e, base = k * nn, side = k * 4 * n;
+        if (!(ep > 0.0)) {
+            for (int s = lane; s < 4 * n; s += 32) {
+                a.Fvtr[side + s] = 0.0;
+                a.Fvtr[KS + side + s] = 0.0;
+                a.Fvtr[2 * KS + side + s] = 0.0;
+                a.Fvtr[3 * KS + side + s] = 0.0;
+            }
+            continue;
+        }
+        double* H = Q[e];
+        double* U = sUV[w][0];
+        double* V = sUV[w][1];
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int node = lane + 32 * r;
+            if (node < nn) {
+                if (EPS_GIVEN) H[node] = a.W[base + node];
+                U[node] = a.uv[base + node];
+                V[node] = a.uv[KN + base + node];
+            }
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int node = lane + 32 * r;
+            if (node >= nn) continue;
+            const int i = node % n, j = node / n;
+            const long long gid = base + node;
+            // BR1 gradient: D along xi and eta plus the interface lift
+            double ux = 0.0, ue = 0.0, vx = 0.0, ve = 0.0;
+#pragma unroll
+            for (int q = 0; q < n; ++q) {
+                const double di = sD[i * n + q], dj = sD[j * n + q];
+                ux = fma(di, U[j * n + q], ux);
+                vx = fma(di, V[j * n + q], vx);
+                ue = fma(dj, U[q * n + i], ue);
+                ve = fma(dj, V[q * n + i], ve);
+            }
+            const double u = U[node], v = V[node];
+            if (i == N) { const long long sl = side + 1 * n + j; ux += iw0 * (a.Ustar[sl] - u); vx += iw0 * (a.Ustar[KS + sl] - v); }
+            if (i == 0) { const long long sl = side + 3 * n + j; ux -= iw0 * (a.Ustar[sl] - u); vx -= iw0 * (a.Ustar[KS + sl] - v); }
+            if (j == N) { const long long sl = side + 2 * n + i; ue += iw0 * (a.Ustar[sl] - u); ve += iw0 * (a.Ustar[KS + sl] - v); }
+            if (j == 0) { const long long sl = side + 0 * n + i; ue -= iw0 * (a.Ustar[sl] - u); ve -= iw0 * (a.Ustar[KS + sl] - v); }
+            const double axx = m.axx[gid], axy = m.axy[gid], aex = m.aex[gid], aey = m.aey[gid];
+            // J grad u = a_xi du/dxi + a_eta du/deta; F^v = h eps grad(.)
+            const double he = H[node] * ep * m.rJ[gid];
+            const double F2 = he * fma(axx, ux, aex * ue);  // h eps U1
+            const double G2 = he * fma(axy, ux, aey * ue);  // h eps U2
+            const double F3 = he * fma(axx, vx, aex * ve);  // h eps V1
+            const double G3 = he * fma(axy, vx, aey * ve);  // h eps V2
+            a.Fvt[gid] = fma(axx, F2, axy * G2);
+            a.Fvt[KN + gid] = fma(axx, F3, axy * G3);
+            a.Fvt[2 * KN + gid] = fma(aex, F2, aey * G2);
+            a.Fvt[3 * KN + gid] = fma(aex, F3, aey * G3);
+            auto put = [&](int f, int p) {
+                const long long sl = side + f * n + p;
+                a.Fvtr[sl] = F2;
+                a.Fvtr[KS + sl] = F3;
+                a.Fvtr[2 * KS + sl] = G2;
+                a.Fvtr[3 * KS + sl] = G3;
             };
-            if (j == 0) zero(0, i);
-            if (i == N) zero(1, j);
-            if (j == N) zero(2, i);
-            if (i == 0) zero(3, j);
+            if (j == 0) put(0, i);
+            if (i == N) put(1, j);
+            if (j == N) put(2, i);
+            if (i == 0) put(3, j);
         }
-        return;
-    }
-    // BR1 gradient: D applied along xi and eta plus the interface lift
-    double ux = 0.0, ue = 0.0, vx = 0.0, ve = 0.0;
-    for (int q = 0; q < n; ++q) {
-        const double di = sh_D[i * n + q], dj = sh_D[j * n + q];
-        ux = fma(di, sh_u[eb + j * n + q], ux);
-        vx = fma(di, sh_v[eb + j * n + q], vx);
-        ue = fma(dj, sh_u[eb + q * n + i], ue);
-        ve = fma(dj, sh_v[eb + q * n + i], ve);
-    }
-    const double u = sh_u[t], v = sh_v[t];
-    if (i == N) { const long long sl = side(1, j); ux += iw0 * (a.Ustar[sl] - u); vx += iw0 * (a.Ustar[KS + sl] - v); }
-    if (i == 0) { const long long sl = side(3, j); ux -= iw0 * (a.Ustar[sl] - u); vx -= iw0 * (a.Ustar[KS + sl] - v); }
-    if (j == N) { const long long sl = side(2, i); ue += iw0 * (a.Ustar[sl] - u); ve += iw0 * (a.Ustar[KS + sl] - v); }
-    if (j == 0) { const long long sl = side(0, i); ue -= iw0 * (a.Ustar[sl] - u); ve -= iw0 * (a.Ustar[KS + sl] - v); }
-    const double axx = m.axx[gid], axy = m.axy[gid], aex = m.aex[gid], aey = m.aey[gid];
-    // J grad u = a_xi du/dxi + a_eta du/deta; F^v = h eps grad(.)
-    const double he = sh_h[t] * ep * m.rJ[gid];
-    const double F2 = he * fma(axx, ux, aex * ue);  // h eps U1
-    const double G2 = he * fma(axy, ux, aey * ue);  // h eps U2
-    const double F3 = he * fma(axx, vx, aex * ve);  // h eps V1
-    const double G3 = he * fma(axy, vx, aey * ve);  // h eps V2
-    const long long KN = m.KN;
-    a.Fvt[gid] = fma(axx, F2, axy * G2);
-    a.Fvt[KN + gid] = fma(axx, F3, axy * G3);
-    a.Fvt[2 * KN + gid] = fma(aex, F2, aey * G2);
-    a.Fvt[3 * KN + gid] = fma(aex, F3, aey * G3);
-    if (bnd) {
-        auto put = [&](int f, int p) {
-            const long long sl = side(f, p);
-            a.Fvtr[sl] = F2;
-            a.Fvtr[KS + sl] = F3;
-            a.Fvtr[2 * KS + sl] = G2;
-            a.Fvtr[3 * KS + sl] = G3;
-        };
-        if (j == 0) put(0, i);
-        if (i == N) put(1, j);
-        if (j == N) put(2, i);
-        if (i == 0) put(3, j);
+        __syncwarp();
     }
 }
 
 template <int N>
-void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s) {
-    constexpr int NE = av_ne<N>();
-    const int threads = ((NE * (N + 1) * (N + 1) + 31) / 32) * 32;
+void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s, bool eps_given) {
+    const int blocks = grid_for(c->m.K, AV_WPB * AV_EPW);
     Timed tm(c, KC_AV, s);
-    k_av<N><<<grid_for(c->m.K, NE), threads, 0, s>>>(a);
+    if (eps_given) k_av<N, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+    else k_av<N, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
 }
 
 }  // namespace
 
 void init_tables_av() { upload_tables(); }
 
-void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
-    AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.eps, c->p.eps0, c->sigma_min,
-             c->sigma_max, stop};
+EpsParams eps_params(const swe_ctx* c) {
+    return EpsParams{c->p.eps0, c->sigma_min, c->sigma_max, pow(10.0, c->sigma_min), pow(10.0, c->sigma_max)};
+}
+
+void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given) {
+    AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.eps, eps_params(c), stop};
     switch (c->m.N) {
-        case 1: av_n<1>(c, a, s); break;
-        case 2: av_n<2>(c, a, s); break;
-        case 3: av_n<3>(c, a, s); break;
-        case 4: av_n<4>(c, a, s); break;
-        case 5: av_n<5>(c, a, s); break;
-        case 6: av_n<6>(c, a, s); break;
-        case 7: av_n<7>(c, a, s); break;
-        case 8: av_n<8>(c, a, s); break;
-        case 9: av_n<9>(c, a, s); break;
-        case 10: av_n<10>(c, a, s); break;
-        case 11: av_n<11>(c, a, s); break;
-        case 12: av_n<12>(c, a, s); break;
+        case 1: av_n<1>(c, a, s, eps_given); break;
+        case 2: av_n<2>(c, a, s, eps_given); break;
+        case 3: av_n<3>(c, a, s, eps_given); break;
+        case 4: av_n<4>(c, a, s, eps_given); break;
+        case 5: av_n<5>(c, a, s, eps_given); break;
+        case 6: av_n<6>(c, a, s, eps_given); break;
+        case 7: av_n<7>(c, a, s, eps_given); break;
+        case 8: av_n<8>(c, a, s, eps_given); break;
+        case 9: av_n<9>(c, a, s, eps_given); break;
+        case 10: av_n<10>(c, a, s, eps_given); break;
+        case 11: av_n<11>(c, a, s, eps_given); break;
+        case 12: av_n<12>(c, a, s, eps_given); break;
         default: break;
     }
 }

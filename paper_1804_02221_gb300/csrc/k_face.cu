@@ -107,10 +107,18 @@ __global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, doubl
 }
 
 // ---------------------------------------------------------------------------
-// Runge-Kutta stage update fused with the positivity limiter (Eq. PosPres)
-// and the h_tol momentum cut; one warp per element, deterministic butterfly
-// reductions. MODE 0: limiter only; 1: 2N-storage stage K = a K + dt R,
-// W = W + b K (K = dt R when a = 0); 2: SSP stage W = a Wn + b (W + dt R).
+// Runge-Kutta stage update fused with the positivity limiter (Eq. PosPres),
+// the h_tol momentum cut and the primitives of the next stage; one warp per
+// element, deterministic butterfly reductions.
+//   MODE 0: limiter only.
+//   MODE 1: 2N-storage stage with the register kept divided by dt:
+//           Kh = a Kh + R (Kh = R when a = 0), W = W + (b dt) Kh.
+//   MODE 2: SSP stage W = a Wn + b (W + dt R).
+// The tests that decide whether an element needs limiting (a node with
+// h < 0), the h_tol cut (h < h_tol) and the non-finite check use the bit
+// patterns of the values (integer comparisons; IEEE doubles other than NaN
+// order like their bit patterns read as sign-magnitude integers), so an
+// element that needs no limiting costs no FP64 instruction beyond the update.
 // ---------------------------------------------------------------------------
 struct UpdArgs {
     DeviceMesh m;
@@ -122,9 +130,12 @@ struct UpdArgs {
     const double* dt_dev;
     int limiter;
     double h_tol;
+    double* uv;  // nullable: write u = hu/h, v = hv/h of the new state
     int* status;
     const int* stop;
 };
+
+constexpr int UPD_WPB = 4;  // warps (elements) per block
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -144,17 +155,31 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// x < 0 (not -0.0) from the bit pattern.
+__device__ __forceinline__ bool is_negative(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return b > 0x8000000000000000ULL;
+}
+
+// Inf or NaN from the bit pattern.
+__device__ __forceinline__ bool non_finite(double x) {
+    return ((unsigned long long)__double_as_longlong(x) & 0x7ff0000000000000ULL) == 0x7ff0000000000000ULL;
+}
+
+// x < t for t > 0 and x not NaN, from the bit patterns.
+__device__ __forceinline__ bool below(double x, long long tbits) {
+    return (long long)__double_as_longlong(x) < tbits;
+}
+
 template <int N, int MODE>
-__global__ void k_update(UpdArgs a) {
+__device__ __forceinline__ void update_element(const UpdArgs& a, long long k, int lane) {
     constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
-    if (stopped(a.stop)) return;
     const DeviceMesh& m = a.m;
-    const int lane = threadIdx.x & 31;
-    const long long k = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (k >= m.K) return;
     const long long KN = m.KN;
     const double dt = a.dt_dev ? *a.dt_dev : a.dt_host;
+    const double bdt = a.b * dt;
     double h[PER], hu[PER], hv[PER];
+    bool neg = false, bad = false;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
         const int node = lane + 32 * r;
@@ -163,19 +188,18 @@ __global__ void k_update(UpdArgs a) {
             const long long gid = k * nn + node;
             double w0 = a.W[gid], w1 = a.W[KN + gid], w2 = a.W[2 * KN + gid];
             if (MODE == 1) {
-                const double r0 = dt * a.R[gid], r1 = dt * a.R[KN + gid], r2 = dt * a.R[2 * KN + gid];
-                double k0v = r0, k1v = r1, k2v = r2;
+                double k0v = a.R[gid], k1v = a.R[KN + gid], k2v = a.R[2 * KN + gid];
                 if (a.a != 0.0) {
-                    k0v = fma(a.a, a.Kreg[gid], r0);
-                    k1v = fma(a.a, a.Kreg[KN + gid], r1);
-                    k2v = fma(a.a, a.Kreg[2 * KN + gid], r2);
+                    k0v = fma(a.a, a.Kreg[gid], k0v);
+                    k1v = fma(a.a, a.Kreg[KN + gid], k1v);
+                    k2v = fma(a.a, a.Kreg[2 * KN + gid], k2v);
                 }
                 a.Kreg[gid] = k0v;
                 a.Kreg[KN + gid] = k1v;
                 a.Kreg[2 * KN + gid] = k2v;
-                w0 = fma(a.b, k0v, w0);
-                w1 = fma(a.b, k1v, w1);
-                w2 = fma(a.b, k2v, w2);
+                w0 = fma(bdt, k0v, w0);
+                w1 = fma(bdt, k1v, w1);
+                w2 = fma(bdt, k2v, w2);
             } else if (MODE == 2) {
                 const double s0 = fma(dt, a.R[gid], w0), s1 = fma(dt, a.R[KN + gid], w1),
                              s2 = fma(dt, a.R[2 * KN + gid], w2);
@@ -186,34 +210,36 @@ __global__ void k_update(UpdArgs a) {
             h[r] = w0;
             hu[r] = w1;
             hv[r] = w2;
+            neg |= is_negative(w0);
+            bad |= non_finite(w0) || non_finite(w1) || non_finite(w2);
         }
     }
-    if (a.limiter) {
-        double s0 = 0.0, s1 = 0.0, s2 = 0.0, mn = INFINITY;
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            if (node < nn) {
-                const double wj = m.wJ[k * nn + node];
-                s0 = fma(wj, h[r], s0);
-                s1 = fma(wj, hu[r], s1);
-                s2 = fma(wj, hv[r], s2);
-                mn = fmin(mn, h[r]);
-            }
-        }
-        const double rv = m.rvol[k];
-        const double m0 = warp_sum(s0) * rv, m1 = warp_sum(s1) * rv, m2 = warp_sum(s2) * rv;
-        mn = warp_min(mn);
+    bad = __any_sync(0xffffffffu, bad);
+    if (bad && (a.limiter || MODE != 0)) {
+        if (lane == 0) atomicOr(a.status, 2);
+    } else if (a.limiter) {
         bool ok = true;
-        if (!isfinite(m0) || !isfinite(m1) || !isfinite(m2)) {
-            if (lane == 0) atomicOr(a.status, 2);
-            ok = false;
-        } else if (m0 < 0.0) {
-            if (lane == 0) atomicOr(a.status, 1);
-            ok = false;
-        }
-        if (ok) {
-            if (mn < 0.0 && m0 - mn > 0.0) {
+        if (__any_sync(0xffffffffu, neg)) {
+            // element needs limiting: J-weighted means and minimum
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0, mn = INFINITY;
+#pragma unroll
+            for (int r = 0; r < PER; ++r) {
+                const int node = lane + 32 * r;
+                if (node < nn) {
+                    const double wj = m.wJ[k * nn + node];
+                    s0 = fma(wj, h[r], s0);
+                    s1 = fma(wj, hu[r], s1);
+                    s2 = fma(wj, hv[r], s2);
+                    mn = fmin(mn, h[r]);
+                }
+            }
+            const double rv = m.rvol[k];
+            const double m0 = warp_sum(s0) * rv, m1 = warp_sum(s1) * rv, m2 = warp_sum(s2) * rv;
+            mn = warp_min(mn);
+            if (m0 < 0.0) {
+                if (lane == 0) atomicOr(a.status, 1);
+                ok = false;
+            } else if (m0 - mn > 0.0) {
                 const double theta = fmin(1.0, m0 / (m0 - mn));
 #pragma unroll
                 for (int r = 0; r < PER; ++r) {
@@ -222,16 +248,13 @@ __global__ void k_update(UpdArgs a) {
                     hv[r] = fma(theta, hv[r] - m2, m2);
                 }
             }
+        }
+        if (ok) {
+            const long long tb = __double_as_longlong(a.h_tol);
 #pragma unroll
             for (int r = 0; r < PER; ++r)
-                if (h[r] < a.h_tol) hu[r] = hv[r] = 0.0;
+                if (below(h[r], tb)) hu[r] = hv[r] = 0.0;
         }
-    } else if (a.status != nullptr && MODE != 0) {
-        double s0 = 0.0;
-#pragma unroll
-        for (int r = 0; r < PER; ++r) s0 += fabs(h[r]) + fabs(hu[r]) + fabs(hv[r]);
-        s0 = warp_sum(s0);
-        if (!isfinite(s0) && lane == 0) atomicOr(a.status, 2);
     }
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
@@ -241,8 +264,22 @@ __global__ void k_update(UpdArgs a) {
             a.W[gid] = h[r];
             a.W[KN + gid] = hu[r];
             a.W[2 * KN + gid] = hv[r];
+            if (a.uv) {
+                const double rh = (long long)__double_as_longlong(h[r]) > 0 ? 1.0 / h[r] : 0.0;
+                a.uv[gid] = hu[r] * rh;
+                a.uv[KN + gid] = hv[r] * rh;
+            }
         }
     }
+}
+
+// One warp per element, blocks looping over the elements (persistent grid).
+template <int N, int MODE>
+__global__ void __launch_bounds__(32 * UPD_WPB) k_update(UpdArgs a) {
+    if (stopped(a.stop)) return;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    for (long long k = (long long)blockIdx.x * UPD_WPB + wid; k < a.m.K; k += (long long)gridDim.x * UPD_WPB)
+        update_element<N, MODE>(a, k, lane);
 }
 
 // ---------------------------------------------------------------------------
@@ -262,13 +299,9 @@ struct DtArgs {
 };
 
 template <int N>
-__global__ void k_dt(DtArgs a) {
+__device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lane) {
     constexpr int n = N + 1, nn = n * n;
-    if (stopped(a.stop)) return;
     const DeviceMesh& m = a.m;
-    const int lane = threadIdx.x & 31;
-    const long long k = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (k >= m.K) return;
     const double g = m.g;
     double lam = 0.0;
     for (int node = lane; node < nn; node += 32) {
@@ -280,7 +313,7 @@ __global__ void k_dt(DtArgs a) {
     }
     lam = warp_max(lam);
     if (lane == 0 && lam > 0.0) atomic_max_pos(&a.bits[0], lam);
-    if (!a.pos) return;
+    if (!a.pos) return;  // uniform: the flag is a kernel argument
     double inv = 0.0;
     for (int sn = lane; sn < 4 * n; sn += 32) {
         const int f = sn / n, p = sn - f * n;
@@ -304,6 +337,14 @@ __global__ void k_dt(DtArgs a) {
     }
     inv = warp_max(inv);
     if (lane == 0 && inv > 0.0) atomic_max_pos(&a.bits[1], inv);
+}
+
+template <int N>
+__global__ void k_dt(DtArgs a) {
+    if (stopped(a.stop)) return;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+    for (long long k = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); k < a.m.K; k += (long long)gridDim.x * wpb)
+        dt_element<N>(a, k, lane);
 }
 
 __global__ void k_dt_final(const unsigned long long* bits, double* dt, double cfl, int N,
@@ -365,29 +406,29 @@ __global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int wh
         for (int c = 0; c < 3; ++c) part[c * RED_BLOCKS + blockIdx.x] = sh[c][0];
 }
 
+// One warp per component: lane sums of a fixed stride, then a fixed butterfly.
 __global__ void k_reduce_final(const double* __restrict__ part, double* __restrict__ out) {
-    if (threadIdx.x < 3) {
-        double s = 0.0;
-        for (int b = 0; b < RED_BLOCKS; ++b) s += part[threadIdx.x * RED_BLOCKS + b];
-        out[threadIdx.x] = s;
-    }
+    const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    double s = 0.0;
+    for (int b = lane; b < RED_BLOCKS; b += 32) s += part[c * RED_BLOCKS + b];
+    s = warp_sum(s);
+    if (lane == 0) out[c] = s;
 }
 
 template <int N>
 void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
-    constexpr int WPB = 4;
-    const int blocks = grid_for(c->m.K, WPB);
+    const int blocks = persistent_grid(c, UPD_WPB);
     Timed tm(c, KC_UPDATE, s);
-    if (mode == 0) k_update<N, 0><<<blocks, 32 * WPB, 0, s>>>(a);
-    else if (mode == 1) k_update<N, 1><<<blocks, 32 * WPB, 0, s>>>(a);
-    else k_update<N, 2><<<blocks, 32 * WPB, 0, s>>>(a);
+    if (mode == 0) k_update<N, 0><<<blocks, 32 * UPD_WPB, 0, s>>>(a);
+    else if (mode == 1) k_update<N, 1><<<blocks, 32 * UPD_WPB, 0, s>>>(a);
+    else k_update<N, 2><<<blocks, 32 * UPD_WPB, 0, s>>>(a);
 }
 
 template <int N>
 void dt_n(swe_ctx* c, const DtArgs& a, cudaStream_t s) {
     constexpr int WPB = 4;
     Timed tm(c, KC_DT, s);
-    k_dt<N><<<grid_for(c->m.K, WPB), 32 * WPB, 0, s>>>(a);
+    k_dt<N><<<persistent_grid(c, WPB), 32 * WPB, 0, s>>>(a);
 }
 
 #define SWE_SWITCH_N(N, CALL)                                                         \
@@ -424,9 +465,9 @@ void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop) {
 }
 
 void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,
-                   const double* dt_dev, cudaStream_t s, const int* stop) {
+                   const double* dt_dev, cudaStream_t s, const int* stop, bool write_uv) {
     UpdArgs u{c->m, W, c->w.R, c->w.Kreg, c->w.Wn, a, b, dt_host, dt_dev, c->p.limiter,
-              c->h_tol, c->w.status, stop};
+              c->h_tol, write_uv ? c->w.uv : nullptr, c->w.status, stop};
 #define SWE_UPD(NN) update_n<NN>(c, mode, u, s)
     SWE_SWITCH_N(c->m.N, SWE_UPD)
 #undef SWE_UPD
@@ -455,7 +496,7 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
     }
     {
         Timed tm(c, KC_REDUCE, s);
-        k_reduce_final<<<1, 32, 0, s>>>(c->w.part, c->w.part + 3 * RED_BLOCKS);
+        k_reduce_final<<<1, 96, 0, s>>>(c->w.part, c->w.part + 3 * RED_BLOCKS);
     }
     cudaMemcpyAsync(host_out, c->w.part + 3 * RED_BLOCKS, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }

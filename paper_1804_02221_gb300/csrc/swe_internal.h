@@ -44,6 +44,12 @@ struct Tables {
 };
 const Tables& tables();
 
+// Parameters of the element viscosity (App. A).
+struct EpsParams {
+    double eps0, smin, smax;
+    double rmin, rmax;  // 10^smin, 10^smax
+};
+
 // Kernel classes for timing.
 enum KernelClass {
     KC_VOLUME = 0,
@@ -77,6 +83,10 @@ struct DeviceMesh {
     const double* nax;  // |a_xi| / J
     const double* nae;  // |a_eta| / J
     const double* rvol; // [K] 1 / sum_ij w_i w_j J
+    const double* fwJ;  // -1 / (w_i w_j J)
+    // Pair constants of the volume kernel, [K][2 directions][N(N+1)/2 pairs][2][n lines]:
+    // w_i w_j D_iq / 4 * (a_i + a_q) for the pair (i, q), i < q, of each line.
+    const double* pm;
     // per unique face node
     const int32_t* f_im;   // owner node id (k*n*n + j*n + i)
     const int32_t* f_ip;   // neighbour node id
@@ -115,6 +125,7 @@ struct Work {
 
 struct swe_ctx {
     int device = 0;
+    int sms = 152;  // multiprocessors of the device (grid size of persistent kernels)
     swe_params p{};
     double sigma_min = 0, sigma_max = 0, h_tol = 1e-4;
     swe::DeviceMesh m{};
@@ -138,12 +149,15 @@ void init_tables_av();
 void launch_prim(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
-void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+EpsParams eps_params(const swe_ctx* c);
+// eps_given: the element viscosities of W are already in the work buffer
+void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given);
 void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop);
-// mode 0: limiter only; 1: 2N-storage stage K = a K + dt R, W += b K;
-// 2: SSP stage W = a Wn + b (W + dt R)
+// mode 0: limiter only; 1: 2N-storage stage Kh = a Kh + R, W += (b dt) Kh
+// (the register holds K/dt); 2: SSP stage W = a Wn + b (W + dt R).
+// write_uv: also write the velocities of the new state into the work buffer.
 void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,
-                   const double* dt_dev, cudaStream_t s, const int* stop);
+                   const double* dt_dev, cudaStream_t s, const int* stop, bool write_uv);
 void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, const int* stop);
 void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
                  const int* stop);
@@ -151,6 +165,16 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
 
 // Record the text of an error for swe_last_error() and return code.
 int set_last_error(int code, const std::string& msg);
+
+// Grid of a warp-per-element kernel whose blocks loop over element groups:
+// at most `per_sm` blocks of `wpb` warps per multiprocessor (the default
+// gives every group its own block, which measured fastest for these
+// short-lived warps), never more blocks than groups.
+inline int persistent_grid(const swe_ctx* c, int wpb, int per_sm = 1 << 20) {
+    const long long groups = (c->m.K + wpb - 1) / wpb;
+    const long long cap = (long long)c->sms * per_sm;
+    return (int)(groups < cap ? (groups > 0 ? groups : 1) : cap);
+}
 
 // Timing bracket of one launch.
 struct Timed {
