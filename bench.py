@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--K1", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--sweep", default=None,
+                    help="comma-separated degrees: one JSON line per degree at ~4.2M nodes "
+                         "(step rate, right-hand-side rates, volume-kernel roofline)")
     return ap.parse_args()
 
 
@@ -118,11 +121,12 @@ def volume_flops_per_node(N):
 
 
 def volume_bytes_per_node(N):
-    """Compulsory DRAM bytes: W (24), velocities (16), contravariant metric
-    vectors (32), 1/J (8), source coefficients (16), R (24), interface flux
-    traces 3 x 4(N+1) doubles per element."""
+    """Compulsory DRAM bytes: W (24), velocities (16), per-pair metric
+    constants (2 doubles per pair, N pairs per node: 16N), -1/(w w J) (8),
+    source coefficients (16), R (24), interface flux traces 3 x 4(N+1) doubles
+    per element."""
     n = N + 1
-    return 120 + 3 * 8 * 4 * n / (n * n)
+    return 88 + 16 * N + 3 * 8 * 4 * n / (n * n)
 
 
 def volume_traffic(N, nodes):
@@ -196,10 +200,69 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def sweep(args):
+    """Degree sweep of the same workload recipe at ~4.2M nodes per degree."""
+    import torch
+
+    from paper_1804_02221_gb300 import inputs as I
+    from paper_1804_02221_gb300 import swedg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    for N in [int(v) for v in args.sweep.split(",")]:
+        K1 = int(round(2048 / (N + 1)))
+        prob = I.dam_break(N=N, K1=K1)
+        kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+        ctx = swedg.SweContext.from_problem(prob, **kw)
+        W0 = torch.from_numpy(prob.W).cuda()
+        W = torch.empty_like(W0)
+        for _ in range(args.warmup):
+            W.copy_(W0)
+            ctx.step(W, 0.0, 1)
+        torch.cuda.synchronize()
+        ctx.timing(True)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            W.copy_(W0)
+            ctx.step(W, 0.0, 1)
+            ctx.integrals(W)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / args.steps
+        vol_ms, vol_n = ctx.timing_read("volume")
+        ctx.timing(False)
+        rates = {}
+        R = torch.empty_like(W0)
+        for name, kk in (("ES+AV", kw), ("EC", dict(flux=0))):
+            c2 = ctx if name == "ES+AV" else swedg.SweContext.from_problem(prob, **kk)
+            for _ in range(2):
+                c2.rhs(W0, R)
+            a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(10):
+                c2.rhs(W0, R)
+            bb.record(stream)
+            torch.cuda.synchronize()
+            rates[name] = prob.nodes / (a.elapsed_time(bb) / 10 * 1e-3)
+            if c2 is not ctx:
+                c2.close()
+        vol = vol_ms / vol_n
+        achieved = volume_flops_per_node(N) * prob.nodes / (vol * 1e-3) / 1e12
+        peak = fp64_peak_gflops(2070.0) / 1e3
+        print(json.dumps({"sweep": True, "N": N, "K": prob.K, "nodes": prob.nodes, "ms_per_step": ms,
+                          "node_updates_per_s": RK_STAGES * prob.nodes / (ms * 1e-3),
+                          "rhs_node_updates_per_s": rates, "volume_ms": vol,
+                          "volume_tflops": achieved, "volume_frac_at_2070MHz": achieved / peak}), flush=True)
+        ctx.close()
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.sweep:
+        sweep(args)
         return
     import numpy as np
     import torch
@@ -230,8 +293,7 @@ def main():
 
     def one_step(Wd):
         ctx.step(Wd, 0.0, 1)
-        ctx.entropy(Wd)
-        ctx.mass(Wd)
+        ctx.integrals(Wd)  # mass, momenta and entropy, read back to the host
 
     for _ in range(args.warmup):
         W.copy_(W0)

@@ -124,6 +124,8 @@ int swe_step(swe_ctx* ctx, double* W, double dt, int nsteps, double* dt_last, vo
  * Host outputs; synchronise `stream`; deterministic summation order. */
 int swe_mass(swe_ctx* ctx, const double* W, double* out3, void* stream);
 int swe_entropy(swe_ctx* ctx, const double* W, double* E, void* stream);
+/* Both in one pass: out4 = (mass, x momentum, y momentum, entropy), host. */
+int swe_integrals(swe_ctx* ctx, const double* W, double* out4, void* stream);
 
 /* Copy the element viscosities epsilon_k (App. A) of the last swe_rhs into
  * device array eps[K]. Asynchronous. */

@@ -316,7 +316,7 @@ extern "C" int swe_create(int N, int K, const double* x, const double* y, const 
     dst = dev_alloc(c, count, e2);                    \
     if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
     AL(W.uv, 2 * KN) AL(W.Fout, 3 * KS) AL(W.Ustar, 2 * KS) AL(W.eps, K) AL(W.Kreg, 3 * KN)
-    AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 3 * 608 + 8) AL(W.dt, 4)
+    AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 4 * 608 + 8) AL(W.dt, 4)
     if (p->av) {
         AL(W.Fvt, 4 * KN) AL(W.Fvtr, 4 * KS) AL(W.Fvout, 2 * KS)
     }
@@ -460,7 +460,7 @@ extern "C" int swe_step(swe_ctx* c, double* W, double dt, int nsteps, double* dt
 extern "C" int swe_mass(swe_ctx* c, const double* W, double* out3, void* stream) {
     if (!c || !W || !out3) return fail(SWE_ERR_ARG, "swe_mass: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    double h[3];
+    double h[4];
     swe::launch_reduce(c, W, 0, h, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "swe_mass");
@@ -471,12 +471,23 @@ extern "C" int swe_mass(swe_ctx* c, const double* W, double* out3, void* stream)
 extern "C" int swe_entropy(swe_ctx* c, const double* W, double* E, void* stream) {
     if (!c || !W || !E) return fail(SWE_ERR_ARG, "swe_entropy: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
-    double h[3];
+    double h[4];
     swe::launch_reduce(c, W, 1, h, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "swe_entropy");
-    *E = h[0];
+    *E = h[3];
     return check_launch("swe_entropy");
+}
+
+extern "C" int swe_integrals(swe_ctx* c, const double* W, double* out4, void* stream) {
+    if (!c || !W || !out4) return fail(SWE_ERR_ARG, "swe_integrals: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    double h[4];
+    swe::launch_reduce(c, W, 2, h, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_integrals");
+    for (int i = 0; i < 4; ++i) out4[i] = h[i];
+    return check_launch("swe_integrals");
 }
 
 extern "C" int swe_get_epsilon(swe_ctx* c, double* eps, void* stream) {

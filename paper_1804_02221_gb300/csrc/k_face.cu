@@ -368,42 +368,45 @@ __global__ void k_copy(long long count, const double* __restrict__ src, double* 
 }
 
 // ---------------------------------------------------------------------------
-// Diagnostics: sum J w w W (what = 0, three sums) or sum J w w e(W) (what = 1,
-// Eq. entropyFunction). Fixed grid, per-block tree sums, then one block adds
-// the partials in order: the result does not depend on scheduling.
+// Diagnostics: sum J w w W (what = 0, three sums), sum J w w e(W) (what = 1,
+// Eq. entropyFunction), or all four (what = 2). Fixed grid, per-block tree
+// sums, then one warp per component adds the partials in a fixed order: the
+// result does not depend on scheduling.
 // ---------------------------------------------------------------------------
 constexpr int RED_BLOCKS = 608;
 constexpr int RED_THREADS = 256;
 
 __global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int what,
                               double* __restrict__ part) {
-    __shared__ double sh[3][RED_THREADS];
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+    __shared__ double sh[4][RED_THREADS];
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
     const double g = m.g;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < m.KN;
          id += (long long)gridDim.x * blockDim.x) {
         const double wj = m.wJ[id], h = W[id], hu = W[m.KN + id], hv = W[2 * m.KN + id];
-        if (what == 0) {
+        if (what != 1) {
             s0 = fma(wj, h, s0);
             s1 = fma(wj, hu, s1);
             s2 = fma(wj, hv, s2);
-        } else {
+        }
+        if (what != 0) {
             const double kin = h > 0.0 ? 0.5 * fma(hu, hu, hv * hv) / h : 0.0;
             const double e = kin + g * h * fma(0.5, h, m.bn[id]);
-            s0 = fma(wj, e, s0);
+            s3 = fma(wj, e, s3);
         }
     }
     sh[0][threadIdx.x] = s0;
     sh[1][threadIdx.x] = s1;
     sh[2][threadIdx.x] = s2;
+    sh[3][threadIdx.x] = s3;
     __syncthreads();
     for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
         if ((int)threadIdx.x < o)
-            for (int c = 0; c < 3; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+            for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
         __syncthreads();
     }
     if (threadIdx.x == 0)
-        for (int c = 0; c < 3; ++c) part[c * RED_BLOCKS + blockIdx.x] = sh[c][0];
+        for (int c = 0; c < 4; ++c) part[c * RED_BLOCKS + blockIdx.x] = sh[c][0];
 }
 
 // One warp per component: lane sums of a fixed stride, then a fixed butterfly.
@@ -496,9 +499,9 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
     }
     {
         Timed tm(c, KC_REDUCE, s);
-        k_reduce_final<<<1, 96, 0, s>>>(c->w.part, c->w.part + 3 * RED_BLOCKS);
+        k_reduce_final<<<1, 128, 0, s>>>(c->w.part, c->w.part + 4 * RED_BLOCKS);
     }
-    cudaMemcpyAsync(host_out, c->w.part + 3 * RED_BLOCKS, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaMemcpyAsync(host_out, c->w.part + 4 * RED_BLOCKS, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
 }  // namespace swe

@@ -105,6 +105,8 @@ def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None):
     (x, y, xw, yw, EToE, EToF, flip) where (xw, yw) are the physical
     coordinates wrapped into the periodic box (identical bit patterns on both
     sides of every face, so fields evaluated there agree across faces).
+    Element k = ky*Kx + kx; with rotate_seed the local frame of every element
+    is turned by a random number of quarter turns.
     """
     x0, x1, y0, y1 = domain
     Lx, Ly = x1 - x0, y1 - y0
@@ -122,60 +124,39 @@ def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None):
     Xcw = np.where(Xc >= x1, Xc - Lx, Xc)
     Ycw = np.where(Yc >= y1, Yc - Ly, Yc)
 
-    x = np.empty((K, n, n))
-    y = np.empty((K, n, n))
-    xw = np.empty((K, n, n))
-    yw = np.empty((K, n, n))
     jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")  # [j, i]
-    for ky in range(Ky):
-        for kx in range(Kx):
-            k = ky * Kx + kx
-            ci, cj = _local_to_canonical(N, int(rot[k]), ii, jj)
-            X, Y = Xc[kx][ci], Yc[ky][cj]
-            XW, YW = Xcw[kx][ci], Ycw[ky][cj]
-            dx, dy = mapping(XW, YW)
-            x[k] = X + dx
-            y[k] = Y + dy
-            xw[k] = XW + dx
-            yw[k] = YW + dy
+    ci_tab = np.stack([_local_to_canonical(N, q, ii, jj)[0] for q in range(4)])  # [4, n, n]
+    cj_tab = np.stack([_local_to_canonical(N, q, ii, jj)[1] for q in range(4)])
+    k = np.arange(K)
+    kx, ky = k % Kx, k // Kx
+    CI, CJ = ci_tab[rot], cj_tab[rot]  # [K, n, n]
+    X = Xc[kx[:, None, None], CI]
+    Y = Yc[ky[:, None, None], CJ]
+    XW = Xcw[kx[:, None, None], CI]
+    YW = Ycw[ky[:, None, None], CJ]
+    dx, dy = mapping(XW, YW)
+    x, y, xw, yw = X + dx, Y + dy, XW + dx, YW + dy
 
-    EToE = np.empty((K, 4), dtype=np.int32)
-    EToF = np.empty((K, 4), dtype=np.int32)
-    flip = np.empty((K, 4), dtype=np.int32)
-    # local face -> canonical face, and whether the local node order runs
-    # against the canonical order along that face
-    canon = np.empty((K, 4), dtype=np.int64)
-    rev = np.empty((K, 4), dtype=bool)
-    for k in range(K):
+    # local face f of a frame turned by q quarter turns lies on canonical face
+    # (f + q) % 4; rev_tab[q, f]: its node order runs against the canonical one
+    rev_tab = np.zeros((4, 4), dtype=bool)
+    for q in range(4):
         for f in range(4):
             li, lj = _face_local_nodes(N, f)
-            ci, cj = _local_to_canonical(N, int(rot[k]), li, lj)
+            ci, cj = _local_to_canonical(N, q, li, lj)
             F = _canonical_face_of(N, ci, cj)
-            canon[k, f] = F
+            assert F == (f + q) % 4
             pos = ci if F in (0, 2) else cj
-            rev[k, f] = pos[0] == N
-    local_of = {}
-    for k in range(K):
-        for f in range(4):
-            local_of[(k, int(canon[k, f]))] = f
-    for ky in range(Ky):
-        for kx in range(Kx):
-            k = ky * Kx + kx
-            for f in range(4):
-                F = int(canon[k, f])
-                if F == 0:
-                    nb = ((ky - 1) % Ky) * Kx + kx
-                elif F == 1:
-                    nb = ky * Kx + (kx + 1) % Kx
-                elif F == 2:
-                    nb = ((ky + 1) % Ky) * Kx + kx
-                else:
-                    nb = ky * Kx + (kx - 1) % Kx
-                Fn = (F + 2) % 4
-                fn = local_of[(nb, Fn)]
-                EToE[k, f] = nb
-                EToF[k, f] = fn
-                flip[k, f] = int(rev[k, f] != rev[nb, fn])
+            rev_tab[q, f] = pos[0] == N
+    f = np.arange(4)[None, :]
+    F = (f + rot[:, None]) % 4  # [K, 4]
+    nkx = np.where(F == 1, (kx[:, None] + 1) % Kx, np.where(F == 3, (kx[:, None] - 1) % Kx, kx[:, None]))
+    nky = np.where(F == 0, (ky[:, None] - 1) % Ky, np.where(F == 2, (ky[:, None] + 1) % Ky, ky[:, None]))
+    nb = nky * Kx + nkx
+    fn = ((F + 2) % 4 - rot[nb]) % 4
+    EToE = nb.astype(np.int32)
+    EToF = fn.astype(np.int32)
+    flip = (rev_tab[rot[:, None], f] != rev_tab[rot[nb], fn]).astype(np.int32)
     return x, y, xw, yw, EToE, EToF, flip
 
 

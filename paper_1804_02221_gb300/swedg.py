@@ -21,7 +21,7 @@ KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "u
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_read",
-           "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc"]
+           "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals"]
 
 
 class Params(ctypes.Structure):
@@ -62,6 +62,7 @@ def lib():
     L.swe_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, dp, vp]
     L.swe_mass.argtypes = [vp, vp, dp, vp]
     L.swe_entropy.argtypes = [vp, vp, dp, vp]
+    L.swe_integrals.argtypes = [vp, vp, dp, vp]
     L.swe_get_epsilon.argtypes = [vp, vp, vp]
     L.swe_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     L.swe_timing.argtypes = [vp, ctypes.c_int]
@@ -179,6 +180,12 @@ class SweContext:
         e = ctypes.c_double()
         _check(lib().swe_entropy(self._h, self._state(W), ctypes.byref(e), _stream(stream)))
         return e.value
+
+    def integrals(self, W, stream=None):
+        """(mass, x momentum, y momentum, entropy) in one pass."""
+        out = (ctypes.c_double * 4)()
+        _check(lib().swe_integrals(self._h, self._state(W), out, _stream(stream)))
+        return np.array(out[:])
 
     def epsilon(self, stream=None):
         import torch

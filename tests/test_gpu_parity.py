@@ -154,8 +154,10 @@ def test_mass_entropy_parity(N):
     assert np.abs(mg - mo).max() < 1e-13 * np.abs(mo).max()
     eo, eg = o.entropy(p.W), g.entropy(Wg)
     assert abs(eg - eo) < 1e-13 * abs(eo)
-    # deterministic: identical on repetition
+    # deterministic: identical on repetition; the combined call agrees
     assert g.entropy(Wg) == eg
+    both = g.integrals(Wg)
+    assert np.array_equal(both[:3], mg) and both[3] == eg
 
 
 def test_step_parity_lake_hump_100_lsrk():
