@@ -44,6 +44,9 @@ def parse():
     ap.add_argument("--K1", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--ensemble", type=int, default=0,
+                    help="members of the uneven ensemble (e.g. 256): one JSON line comparing the batched "
+                         "ensemble with stepping every member through its own context")
     ap.add_argument("--sweep", default=None,
                     help="comma-separated degrees: one JSON line per degree at ~4.2M nodes "
                          "(step rate, right-hand-side rates, volume-kernel roofline)")
@@ -156,6 +159,20 @@ def fp64_peak_gflops(sm_mhz):
     return 152 * 2 * 2 * sm_mhz * 1e6 / 1e9
 
 
+def combine_ranks(ms_step, e2e_ms, nodes, world_size, dist=None, device="cpu"):
+    """Replicas: every rank advanced its own mesh of `nodes` nodes. The step
+    time is the maximum over ranks and the value the work of all ranks over
+    that time. Returns (ms_step, e2e_ms, value, e2e_value)."""
+    import torch
+    if dist is not None and world_size > 1:
+        t = torch.tensor([ms_step, e2e_ms], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms_step, e2e_ms = float(t[0]), float(t[1])
+    value = world_size * RK_STAGES * nodes / (ms_step * 1e-3)
+    e2e_value = world_size * RK_STAGES * nodes / (e2e_ms * 1e-3)
+    return ms_step, e2e_ms, value, e2e_value
+
+
 # ---------------------------------------------------------------------------
 # Oracle timing (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------
@@ -256,6 +273,82 @@ def sweep(args):
         ctx.close()
 
 
+def ensemble_bench(args):
+    """The uneven ensemble (16x16..96x96 quads, N in {3, 5, 7}): `steps`
+    adaptive LSRK4(5) steps of all members in one swe_ens_step call (one graph
+    replay per step) against the plain path, every member advanced by its own
+    context in its own swe_step call. Same members, same parameters, the same
+    results bit for bit."""
+    import torch
+
+    from paper_1804_02221_gb300 import inputs as I
+    from paper_1804_02221_gb300 import swedg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    t0 = time.perf_counter()
+    probs = I.ensemble(args.ensemble)
+    t_gen = time.perf_counter() - t0
+    kw = dict(flux=1, av=True, eps0=0.01, limiter=True, rk=0, cfl=0.5)
+    nodes = sum(p.nodes for p in probs)
+    t0 = time.perf_counter()
+    ens = swedg.SweEnsemble(probs, **kw)
+    t_create = time.perf_counter() - t0
+    W0 = ens.pack([p.W for p in probs])
+    W = torch.empty_like(W0)
+
+    def timed(fn):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        a.record(stream)
+        fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b)
+
+    W.copy_(W0)
+    ens.step(W, 0.0, args.warmup)
+    W.copy_(W0)
+    l0 = ens.launches()
+    ms_ens = timed(lambda: ens.step(W, 0.0, args.steps)) / args.steps
+    launches_ens = ens.launches() - l0
+    Wens = W.clone()
+    R = torch.empty_like(W0)
+    ens.rhs(W0, R)
+    ms_rhs_ens = timed(lambda: [ens.rhs(W0, R) for _ in range(5)]) / 5
+
+    ctxs = [swedg.SweContext.from_problem(p, **kw) for p in probs]
+    Ws = [torch.from_numpy(p.W).cuda() for p in probs]
+    for c, w in zip(ctxs, Ws):
+        c.step(w, 0.0, args.warmup)
+    for w, p in zip(Ws, probs):
+        w.copy_(torch.from_numpy(p.W))
+    l0 = sum(c.launches() for c in ctxs)
+    ms_plain = timed(lambda: [c.step(w, 0.0, args.steps) for c, w in zip(ctxs, Ws)]) / args.steps
+    launches_plain = sum(c.launches() for c in ctxs) - l0
+    same = all(torch.equal(ens.view(Wens, i), Ws[i]) for i in range(len(probs)))
+    Rs = [torch.empty_like(w) for w in Ws]
+    Wi = [torch.from_numpy(p.W).cuda() for p in probs]
+    ms_rhs_plain = timed(lambda: [[c.rhs(w, r) for c, w, r in zip(ctxs, Wi, Rs)] for _ in range(5)]) / 5
+    rate = lambda ms: RK_STAGES * nodes / (ms * 1e-3)
+    line = {
+        "ensemble": True, "metric": "RHS node-updates/s (FP64)", "unit": "node-updates/s",
+        "members": len(probs), "nodes": nodes, "groups": ens.ngroups,
+        "degrees": {str(N): sum(1 for p in probs if p.N == N) for N in sorted({p.N for p in probs})},
+        "steps": args.steps, "warmup": args.warmup,
+        "batched": {"value": rate(ms_ens), "ms_per_step": ms_ens, "gpu_launches": launches_ens,
+                    "rhs_node_updates_per_s": nodes / (ms_rhs_ens * 1e-3)},
+        "plain": {"value": rate(ms_plain), "ms_per_step": ms_plain, "gpu_launches": launches_plain,
+                  "rhs_node_updates_per_s": nodes / (ms_rhs_plain * 1e-3)},
+        "speedup": ms_plain / ms_ens, "bitwise_equal": same,
+        "setup_s": {"inputs": t_gen, "create": t_create},
+        "config": {"workload": f"uneven ensemble: {len(probs)} members, 16x16..96x96 curved periodic quads, "
+                               "N in {3,5,7}, seeded 8-Gaussian bathymetry + Gaussian hump, ES+AV(eps0=0.01)"
+                               "+limiter, adaptive LSRK4(5) CFL 0.5",
+                   "l2": "inputs larger than L2 (~0.95 GB state)"},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -263,6 +356,9 @@ def main():
         return
     if args.sweep:
         sweep(args)
+        return
+    if args.ensemble:
+        ensemble_bench(args)
         return
     import numpy as np
     import torch
@@ -357,13 +453,7 @@ def main():
         rhs_rates[name] = nodes / (a.elapsed_time(b) / 10 * 1e-3)
 
     # ---- reduce over ranks ----
-    t_step = ms
-    if dist is not None:
-        tt = torch.tensor([ms, e2e_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_step, e2e_ms = float(tt[0]), float(tt[1])
-    value = ws * RK_STAGES * nodes / (t_step * 1e-3)
-    e2e_value = ws * RK_STAGES * nodes / (e2e_ms * 1e-3)
+    t_step, e2e_ms, value, e2e_value = combine_ranks(ms, e2e_ms, nodes, ws, dist, "cuda")
 
     if rank != 0:
         if dist is not None:

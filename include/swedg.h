@@ -176,6 +176,77 @@ int swe_info(const swe_ctx* ctx, int* N, int* K, int* nfaces);
 int swe_integrals_noalloc(int N, int K, const double* W, const double* wJ, const double* b, double g,
                           double* out4, void* stream);
 
+/* ---------------------------------------------------------------------------
+ * Ensembles: many independent periodic meshes, of mixed degree and size,
+ * advanced together (the paper runs one mesh per launch; this batched form,
+ * with its layout, is this library's own). Each instance is the problem of
+ * swe_create: its own mesh, bathymetry and state, the shared g and
+ * parameters, and its own time step.
+ *
+ * State layout of an ensemble: one device buffer of swe_ens_size doubles.
+ * The instances of one degree form a group; a group's planes h, hu, hv each
+ * hold the [K][n][n] nodes of its instances back to back (in instance order),
+ * and group planes start on 256-byte boundaries. swe_ens_layout gives, for
+ * instance i, the offset (doubles) of its h nodes and the plane stride, so
+ * that its (h, hu, hv) planes start at W + offset + c*plane_stride and are
+ * laid out as in a single context.
+ *
+ * Every kernel evaluates each element, face and node exactly as it does for a
+ * single context, so an instance's right-hand side and steps are bitwise
+ * those of swe_create/swe_rhs/swe_step on that instance alone. */
+typedef struct swe_ens swe_ens;
+
+/* One instance (host arrays, copied at creation; layout as for swe_create).
+ * EToE is local to the instance: 0 <= EToE < K. */
+typedef struct {
+    int N;
+    int K;
+    const double* x;
+    const double* y;
+    const double* b;
+    const int32_t* EToE;
+    const int32_t* EToF;
+    const int32_t* flip;
+} swe_instance;
+
+/* Build an ensemble of ninst >= 1 instances on the current CUDA device, with
+ * gravity g and parameters p shared by all. Errors as swe_create (the text
+ * names the failing degree group); SWE_ERR_ARG also for EToE outside an
+ * instance. */
+int swe_ens_create(int ninst, const swe_instance* inst, double g, const swe_params* p, swe_ens** out);
+void swe_ens_destroy(swe_ens* ens);
+
+/* Doubles of an ensemble state (total) and the number of degree groups. */
+int swe_ens_size(const swe_ens* ens, int64_t* total, int* ngroups);
+/* Where instance i lives in an ensemble state (see above), its N and K. */
+int swe_ens_layout(const swe_ens* ens, int i, int64_t* offset, int64_t* plane_stride, int* N, int* K);
+
+/* swe_rhs of every instance: W, R device buffers of swe_ens_size doubles, not
+ * overlapping. Asynchronous on `stream`. */
+int swe_ens_rhs(swe_ens* ens, const double* W, double* R, void* stream);
+
+/* swe_max_dt of every instance: host outputs dt_cfl[ninst], dt_pos[ninst]
+ * (nullable). Synchronises `stream`. */
+int swe_ens_max_dt(swe_ens* ens, const double* W, double* dt_cfl, double* dt_pos, void* stream);
+
+/* swe_step of every instance (dt <= 0: each instance takes its own
+ * min(dt_cfl, dt_pos) at the start of every step). One step of all groups is
+ * a CUDA graph, captured at the first call for a given (W, dt) and replayed
+ * nsteps times on `stream`. The status is shared: if any instance fails
+ * (negative mean or non-finite value), every instance is restored to the
+ * start of the failing step and SWE_ERR_NEG_MEAN or SWE_ERR_NONFINITE is
+ * returned. dt_last (host [ninst], nullable) receives each instance's last
+ * step size. Synchronises `stream`. */
+int swe_ens_step(swe_ens* ens, double* W, double dt, int nsteps, double* dt_last, void* stream);
+
+/* swe_integrals of every instance: out (host [ninst][4]) = (mass, x momentum,
+ * y momentum, entropy) per instance, in a fixed summation order.
+ * Synchronises `stream`. */
+int swe_ens_integrals(swe_ens* ens, const double* W, double* out, void* stream);
+
+/* Kernels launched so far (graph replays count their kernels). */
+int64_t swe_ens_launches(const swe_ens* ens);
+
 /* Text of the last error on the calling thread ("" if none). */
 const char* swe_last_error(void);
 

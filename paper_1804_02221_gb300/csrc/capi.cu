@@ -106,10 +106,14 @@ Timed::~Timed() {
 // Context
 // ---------------------------------------------------------------------------
 
-extern "C" int swe_create(int N, int K, const double* x, const double* y, const int32_t* EToE,
-                          const int32_t* EToF, const int32_t* flip, const double* b, double g,
-                          const swe_params* p, swe_ctx** out) {
-    using namespace swe;
+namespace swe {
+
+// Context construction shared by swe_create and the ensembles: inst (host,
+// nullable) gives the instance index of every element (ninst instances);
+// shared_status (device, nullable) replaces the context's own status word.
+int create_ctx(int N, int K, const double* x, const double* y, const int32_t* EToE, const int32_t* EToF,
+               const int32_t* flip, const double* b, double g, const swe_params* p, const int32_t* inst,
+               int ninst, int* shared_status, swe_ctx** out) {
     if (!out) return fail(SWE_ERR_ARG, "swe_create: out is NULL");
     *out = nullptr;
     if (!x || !y || !EToE || !EToF || !flip || !b || !p)
@@ -311,25 +315,41 @@ extern "C" int swe_create(int N, int K, const double* x, const double* y, const 
     UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
 #undef UP
     m.nae = nullptr;
+    m.inst = nullptr;
+    m.ninst = 1;
+    if (inst) {
+        std::vector<int32_t> iv(inst, inst + K);
+        for (int32_t v : iv)
+            if (v < 0 || v >= ninst) {
+                free_all(c);
+                delete c;
+                return fail(SWE_ERR_ARG, "swe_create: instance index out of range");
+            }
+        m.inst = dev_upload(c, iv, e2);
+        if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: upload"); }
+        m.ninst = ninst;
+    }
     Work& W = c->w;
 #define AL(dst, count)                                \
     dst = dev_alloc(c, count, e2);                    \
     if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
     AL(W.uv, 2 * KN) AL(W.Fout, 3 * KS) AL(W.Ustar, 2 * KS) AL(W.eps, K) AL(W.Kreg, 3 * KN)
-    AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 4 * 608 + 8) AL(W.dt, 4)
+    AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 4 * 608 + 8) AL(W.dt, 3 * (size_t)m.ninst + 1)
     if (p->av) {
         AL(W.Fvt, 4 * KN) AL(W.Fvtr, 4 * KS) AL(W.Fvout, 2 * KS)
     }
 #undef AL
     {
         void* q = nullptr;
-        e2 = cudaMalloc(&q, 2 * sizeof(unsigned long long) + 16);
+        e2 = cudaMalloc(&q, 2 * sizeof(unsigned long long) * m.ninst + 16);
         if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
         c->allocations.push_back(q);
         W.dtbits = static_cast<unsigned long long*>(q);
-        W.status = reinterpret_cast<int*>(static_cast<char*>(q) + 2 * sizeof(unsigned long long));
+        W.status = reinterpret_cast<int*>(static_cast<char*>(q) + 2 * sizeof(unsigned long long) * m.ninst);
+        if (shared_status) W.status = shared_status;
     }
-    cudaMemset(W.status, 0, sizeof(int));
+    if (!shared_status) cudaMemset(W.status, 0, sizeof(int));
+    swe::prepare_volume(c);
     cudaMemset(W.eps, 0, sizeof(double) * K);
     e2 = cudaDeviceSynchronize();
     if (e2 != cudaSuccess) {
@@ -339,6 +359,14 @@ extern "C" int swe_create(int N, int K, const double* x, const double* y, const 
     }
     *out = c;
     return SWE_OK;
+}
+
+}  // namespace swe
+
+extern "C" int swe_create(int N, int K, const double* x, const double* y, const int32_t* EToE,
+                          const int32_t* EToF, const int32_t* flip, const double* b, double g,
+                          const swe_params* p, swe_ctx** out) {
+    return swe::create_ctx(N, K, x, y, EToE, EToF, flip, b, g, p, nullptr, 1, nullptr, out);
 }
 
 extern "C" void swe_destroy(swe_ctx* c) {
@@ -352,20 +380,38 @@ extern "C" void swe_destroy(swe_ctx* c) {
 // Right-hand side
 // ---------------------------------------------------------------------------
 
-namespace {
+namespace swe {
 
-// prim_done: the velocities of W are in the work buffer (written by the
-// previous stage update); eps_done: so are its element viscosities.
 void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done,
-               bool eps_done = false) {
-    if (!prim_done) swe::launch_prim(c, W, s, stop);
-    swe::launch_surface(c, W, s, stop);
+               bool eps_done) {
+    if (!prim_done) launch_prim(c, W, s, stop);
+    launch_surface(c, W, s, stop);
     if (c->p.av) {
-        swe::launch_av(c, W, s, stop, eps_done);
-        swe::launch_visc_face(c, s, stop);
+        launch_av(c, W, s, stop, eps_done);
+        launch_visc_face(c, s, stop);
     }
-    swe::launch_volume(c, W, R, s, stop);
+    launch_volume(c, W, R, s, stop);
 }
+
+void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop, bool save) {
+    const bool adaptive = !(dt > 0.0);
+    const double* dtd = adaptive ? c->w.dt : nullptr;
+    if (save) launch_copy(c, W, c->w.Wn, 3 * c->m.KN, s, stop);
+    if (adaptive) launch_dt(c, W, 0.0, s, stop);
+    const int stages = c->p.rk == 0 ? 5 : 3;
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    for (int stage = 0; stage < stages; ++stage) {
+        rhs_chain(c, W, c->w.R, s, stop, true);
+        if (c->p.rk == 0)
+            launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop, true);
+        else
+            launch_update(c, 2, W, ca[stage], cb[stage], dt, dtd, s, stop, true);
+    }
+}
+
+}  // namespace swe
+
+namespace {
 
 int check_launch(const char* where) {
     cudaError_t e = cudaGetLastError();
@@ -377,7 +423,7 @@ int check_launch(const char* where) {
 extern "C" int swe_rhs(swe_ctx* c, const double* W, double* R, void* stream) {
     if (!c || !W || !R) return fail(SWE_ERR_ARG, "swe_rhs: NULL argument");
     if (W == R) return fail(SWE_ERR_ARG, "swe_rhs: W and R must not overlap");
-    rhs_chain(c, W, R, (cudaStream_t)stream, nullptr, false);
+    swe::rhs_chain(c, W, R, (cudaStream_t)stream, nullptr, false);
     return check_launch("swe_rhs");
 }
 
@@ -411,28 +457,11 @@ extern "C" int swe_step(swe_ctx* c, double* W, double dt, int nsteps, double* dt
     const int* stop = c->w.status;
     const long long n3 = 3 * c->m.KN;
     const bool adaptive = !(dt > 0.0);
-    const double* dtd = adaptive ? c->w.dt : nullptr;
     cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
     // Every stage update also writes the velocities of its new state, so only
     // the first stage of the call needs the primitives kernel.
-    bool uv_valid = false;
-    for (int st = 0; st < nsteps; ++st) {
-        swe::launch_copy(c, W, c->w.Wn, n3, s, stop);
-        if (!uv_valid) {
-            swe::launch_prim(c, W, s, stop);
-            uv_valid = true;
-        }
-        if (adaptive) swe::launch_dt(c, W, 0.0, s, stop);
-        const int stages = c->p.rk == 0 ? 5 : 3;
-        const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
-        for (int stage = 0; stage < stages; ++stage) {
-            rhs_chain(c, W, c->w.R, s, stop, true);
-            if (c->p.rk == 0)
-                swe::launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop, true);
-            else
-                swe::launch_update(c, 2, W, ca[stage], cb[stage], dt, dtd, s, stop, true);
-        }
-    }
+    if (nsteps > 0) swe::launch_prim(c, W, s, stop);
+    for (int st = 0; st < nsteps; ++st) swe::step_once(c, W, dt, s, stop);
     int rc = check_launch("swe_step");
     if (rc) return rc;
     int status = 0;

@@ -176,7 +176,7 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, in
     constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
     const DeviceMesh& m = a.m;
     const long long KN = m.KN;
-    const double dt = a.dt_dev ? *a.dt_dev : a.dt_host;
+    const double dt = a.dt_dev ? a.dt_dev[m.inst ? m.inst[k] : 0] : a.dt_host;
     const double bdt = a.b * dt;
     double h[PER], hu[PER], hv[PER];
     bool neg = false, bad = false;
@@ -312,7 +312,8 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
         lam = fmax(lam, fma(c, a.cfl_n[id], m.rJ[id] * vel));
     }
     lam = warp_max(lam);
-    if (lane == 0 && lam > 0.0) atomic_max_pos(&a.bits[0], lam);
+    unsigned long long* bits = a.bits + 2 * (m.inst ? m.inst[k] : 0);
+    if (lane == 0 && lam > 0.0) atomic_max_pos(&bits[0], lam);
     if (!a.pos) return;  // uniform: the flag is a kernel argument
     double inv = 0.0;
     for (int sn = lane; sn < 4 * n; sn += 32) {
@@ -336,7 +337,7 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
         if (hm > 0.0 && B * jump < 0.0) inv = fmax(inv, fabs(ca * B * jump) * rwa / (g * hm));
     }
     inv = warp_max(inv);
-    if (lane == 0 && inv > 0.0) atomic_max_pos(&a.bits[1], inv);
+    if (lane == 0 && inv > 0.0) atomic_max_pos(&bits[1], inv);
 }
 
 template <int N>
@@ -347,16 +348,19 @@ __global__ void k_dt(DtArgs a) {
         dt_element<N>(a, k, lane);
 }
 
-__global__ void k_dt_final(const unsigned long long* bits, double* dt, double cfl, int N,
+// One thread per instance: dt[i] in use, dt[ninst + i] CFL, dt[2 ninst + i] positivity.
+__global__ void k_dt_final(const unsigned long long* bits, double* dt, int ninst, double cfl, int N,
                            double dt_fixed, const int* stop) {
     if (stopped(stop)) return;
-    const double lam = __longlong_as_double((long long)bits[0]);
-    const double inv = __longlong_as_double((long long)bits[1]);
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= ninst) return;
+    const double lam = __longlong_as_double((long long)bits[2 * i]);
+    const double inv = __longlong_as_double((long long)bits[2 * i + 1]);
     const double dtc = lam > 0.0 ? cfl * 2.0 / (N + 1.0) / lam : INFINITY;
     const double dtp = inv > 0.0 ? 1.0 / inv : INFINITY;
-    dt[1] = dtc;
-    dt[2] = dtp;
-    dt[0] = dt_fixed > 0.0 ? dt_fixed : fmin(dtc, dtp);
+    dt[ninst + i] = dtc;
+    dt[2 * ninst + i] = dtp;
+    dt[i] = dt_fixed > 0.0 ? dt_fixed : fmin(dtc, dtp);
 }
 
 __global__ void k_copy(long long count, const double* __restrict__ src, double* __restrict__ dst,
@@ -418,6 +422,37 @@ __global__ void k_reduce_final(const double* __restrict__ part, double* __restri
     if (lane == 0) out[c] = s;
 }
 
+// Per-instance integrals of an ensemble group: block i sums the nodes of
+// elements [ebeg[i], ebeg[i+1]) into out[4 i .. 4 i + 3] (mass, momenta,
+// entropy), in a fixed order.
+__global__ void k_reduce_inst(DeviceMesh m, const double* __restrict__ W, const long long* __restrict__ ebeg,
+                              double* __restrict__ out) {
+    __shared__ double sh[4][RED_THREADS];
+    const long long nn = (long long)m.n * m.n;
+    const long long lo = ebeg[blockIdx.x] * nn, hi = ebeg[blockIdx.x + 1] * nn;
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    const double g = m.g;
+    for (long long id = lo + threadIdx.x; id < hi; id += blockDim.x) {
+        const double wj = m.wJ[id], h = W[id], hu = W[m.KN + id], hv = W[2 * m.KN + id];
+        s0 = fma(wj, h, s0);
+        s1 = fma(wj, hu, s1);
+        s2 = fma(wj, hv, s2);
+        const double kin = h > 0.0 ? 0.5 * fma(hu, hu, hv * hv) / h : 0.0;
+        s3 = fma(wj, kin + g * h * fma(0.5, h, m.bn[id]), s3);
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    sh[2][threadIdx.x] = s2;
+    sh[3][threadIdx.x] = s3;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int c = 0; c < 4; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x < 4) out[4 * blockIdx.x + threadIdx.x] = sh[threadIdx.x][0];
+}
+
 template <int N>
 void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
     const int blocks = persistent_grid(c, UPD_WPB);
@@ -477,13 +512,14 @@ void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double d
 }
 
 void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, const int* stop) {
-    cudaMemsetAsync(c->w.dtbits, 0, 2 * sizeof(unsigned long long), s);
+    cudaMemsetAsync(c->w.dtbits, 0, 2 * sizeof(unsigned long long) * c->m.ninst, s);
     DtArgs a{c->m, W, c->w.uv, c->m.nax, (c->p.limiter && c->p.flux) ? 1 : 0, c->w.dtbits, stop};
 #define SWE_DT(NN) dt_n<NN>(c, a, s)
     SWE_SWITCH_N(c->m.N, SWE_DT)
 #undef SWE_DT
     Timed tm(c, KC_DT, s);
-    k_dt_final<<<1, 1, 0, s>>>(c->w.dtbits, c->w.dt, c->p.cfl, c->m.N, dt_fixed, stop);
+    k_dt_final<<<(c->m.ninst + 127) / 128, 128, 0, s>>>(c->w.dtbits, c->w.dt, c->m.ninst, c->p.cfl, c->m.N,
+                                                          dt_fixed, stop);
 }
 
 void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
@@ -502,6 +538,11 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
         k_reduce_final<<<1, 128, 0, s>>>(c->w.part, c->w.part + 4 * RED_BLOCKS);
     }
     cudaMemcpyAsync(host_out, c->w.part + 4 * RED_BLOCKS, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+void launch_reduce_inst(swe_ctx* c, const double* W, const long long* ebeg, double* out, cudaStream_t s) {
+    Timed tm(c, KC_REDUCE, s);
+    k_reduce_inst<<<c->m.ninst, RED_THREADS, 0, s>>>(c->m, W, ebeg, out);
 }
 
 }  // namespace swe

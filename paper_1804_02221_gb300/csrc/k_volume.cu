@@ -242,15 +242,23 @@ __global__ void __launch_bounds__(vol_ne<N>() * (N + 1)) k_volume(VolArgs a) {
     }
 }
 
+// Opt in to the kernel's shared memory once per process (before any stream
+// capture: contexts call it at creation).
+template <int N, bool AV>
+void set_attr() {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_volume<N, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)vol_smem<N, AV>());
+        attr = true;
+    }
+}
+
 template <int N, bool AV>
 void launch_n(swe_ctx* c, const VolArgs& a, cudaStream_t s) {
     constexpr int NE = vol_ne<N>();
     constexpr size_t smem = vol_smem<N, AV>();
-    static bool attr = false;
-    if (!attr) {
-        cudaFuncSetAttribute(k_volume<N, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        attr = true;
-    }
+    set_attr<N, AV>();
     const int blocks = grid_for(c->m.K, NE);
     Timed tm(c, KC_VOLUME, s);
     k_volume<N, AV><<<blocks, NE * (N + 1), smem, s>>>(a);
@@ -259,6 +267,21 @@ void launch_n(swe_ctx* c, const VolArgs& a, cudaStream_t s) {
 }  // namespace
 
 void init_tables_volume() { upload_tables(); }
+
+void prepare_volume(swe_ctx* c) {
+#define SWE_VOL_ATTR(NN)           \
+    case NN:                       \
+        set_attr<NN, true>();      \
+        set_attr<NN, false>();     \
+        break;
+    switch (c->m.N) {
+        SWE_VOL_ATTR(1) SWE_VOL_ATTR(2) SWE_VOL_ATTR(3) SWE_VOL_ATTR(4)
+        SWE_VOL_ATTR(5) SWE_VOL_ATTR(6) SWE_VOL_ATTR(7) SWE_VOL_ATTR(8)
+        SWE_VOL_ATTR(9) SWE_VOL_ATTR(10) SWE_VOL_ATTR(11) SWE_VOL_ATTR(12)
+        default: break;
+    }
+#undef SWE_VOL_ATTR
+}
 
 void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop) {
     VolArgs a{c->m, W, c->w.uv, c->w.Fout, c->w.Fvt, c->w.Fvout, c->w.eps, R, stop};

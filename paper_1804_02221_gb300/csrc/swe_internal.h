@@ -102,6 +102,9 @@ struct DeviceMesh {
     const double* s_nx;    // own outward unit normal
     const double* s_ny;
     const double* s_rwa;   // 1/(omega_0 a), a = J/Jsurf (Lemma PosPres)
+    // ensembles: instance of every element (nullable: one instance), count
+    const int32_t* inst;
+    int ninst;
 };
 
 struct Work {
@@ -116,9 +119,9 @@ struct Work {
     double* Wn;     // [3][KN] state at the start of a step
     double* R;      // [3][KN] right-hand side of the current stage
     double* part;   // reduction partials
-    double* dt;     // [4]: dt in use, dt_cfl, dt_pos
-    unsigned long long* dtbits;  // [2]: max of lambda/J, max of inverse positivity dt
-    int* status;    // [1] status bits
+    double* dt;     // [3][ninst]: dt in use, dt_cfl, dt_pos of every instance
+    unsigned long long* dtbits;  // [ninst][2]: max of lambda/J, max of inverse positivity dt
+    int* status;    // [1] status bits (shared by the groups of an ensemble)
 };
 
 }  // namespace swe
@@ -146,6 +149,10 @@ void init_tables_volume();
 void init_tables_face();
 void init_tables_av();
 
+// Per-process kernel attributes of the context's degree (called at creation,
+// so that later launches, also inside a stream capture, change no state).
+void prepare_volume(swe_ctx* c);
+
 void launch_prim(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
@@ -162,6 +169,28 @@ void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, con
 void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
                  const int* stop);
 void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cudaStream_t s);
+// Per-instance (mass, momenta, entropy) of an ensemble group into device
+// out[4 * ninst]; ebeg (device, ninst + 1) holds the element ranges.
+void launch_reduce_inst(swe_ctx* c, const double* W, const long long* ebeg, double* out, cudaStream_t s);
+
+// One right-hand side R(W) (prim_done: the velocities of W are already in
+// the work buffer, written by the previous stage update; eps_done: so are its
+// element viscosities).
+void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done,
+               bool eps_done = false);
+// One Runge-Kutta step of W (dt <= 0: adaptive, from the device time step of
+// every instance). Expects the velocities of W in the work buffer and leaves
+// those of the new state there. save: first copy the start state to w.Wn
+// (callers that run several contexts concurrently on one status word make
+// all those copies before any of the steps, so that a failure in one
+// context cannot stop another's copy).
+void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop, bool save = true);
+
+// Context construction (swe_create; ensembles pass an instance map and a
+// status word shared by their groups).
+int create_ctx(int N, int K, const double* x, const double* y, const int32_t* EToE, const int32_t* EToF,
+               const int32_t* flip, const double* b, double g, const swe_params* p, const int32_t* inst,
+               int ninst, int* shared_status, swe_ctx** out);
 
 // Record the text of an error for swe_last_error() and return code.
 int set_last_error(int code, const std::string& msg);

@@ -180,6 +180,16 @@ def _gaussian_sum_periodic(xw, yw, a, c, s, Lx, Ly):
     return B
 
 
+def _gaussian_sum_periodic_separable(xw, yw, a, c, s, Lx, Ly):
+    """The same sum of periodic Gaussian images, factored per direction."""
+    B = np.zeros_like(xw)
+    for ak, ck, sk in zip(a, c, s):
+        ex = sum(np.exp(-((xw - ck[0] - sx) / sk) ** 2) for sx in (-Lx, 0.0, Lx))
+        ey = sum(np.exp(-((yw - ck[1] - sy) / sk) ** 2) for sy in (-Ly, 0.0, Ly))
+        B += ak * ex * ey
+    return B
+
+
 def _smooth_periodic_field(rng, xw, yw, Lx, Ly, modes=3):
     """Random smooth periodic field of unit-order amplitude."""
     f = np.zeros_like(xw)
@@ -301,6 +311,32 @@ def random_rough(N=3, K1=4, seed=0, rotate_seed=None, g=9.81, dry_fraction=0.0) 
     p.W = _state(h, u, v)
     p.name = "random_rough"
     return p
+
+
+def ensemble_member(i: int, seed=5, sizes=(16, 96), degrees=(3, 5, 7), g=9.81) -> Problem:
+    """Member i of the uneven ensemble: degree drawn from `degrees`, an s x s
+    curved periodic [0,2]^2 mesh with s uniform in `sizes` (inclusive), a
+    bathymetry 0.3 B/max B with B a sum of 8 seeded Gaussians, and a lake at
+    rest h + b = 1 with a Gaussian hump (amplitude 0.1, width 0.2)."""
+    rng = np.random.default_rng([seed, i])
+    N = int(rng.choice(np.asarray(degrees)))
+    s = int(rng.integers(sizes[0], sizes[1] + 1))
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, s, s, (0.0, 2.0, 0.0, 2.0), _sine_map(0.05, math.pi))
+    a = rng.uniform(0.2, 1.0, size=8)
+    c = rng.uniform(0.0, 2.0, size=(8, 2))
+    w = rng.uniform(0.1, 0.4, size=8)
+    B = _gaussian_sum_periodic_separable(xw, yw, a, c, w, 2.0, 2.0)
+    b = 0.3 * B / B.max()
+    c0 = rng.uniform(0.5, 1.5, size=2)
+    h = 1.0 - b + 0.1 * np.exp(-((xw - c0[0]) ** 2 + (yw - c0[1]) ** 2) / 0.2 ** 2)
+    z = np.zeros_like(h)
+    return Problem("ensemble_member", N, s, s, x, y, b, _state(h, z, z), E, F, fl, g,
+                   {"member": i, "seed": seed})
+
+
+def ensemble(ninst=256, seed=5, sizes=(16, 96), degrees=(3, 5, 7), g=9.81) -> list:
+    """The uneven ensemble: `ninst` independent members (see ensemble_member)."""
+    return [ensemble_member(i, seed, sizes, degrees, g) for i in range(ninst)]
 
 
 CONFIGS = {

@@ -21,7 +21,9 @@ KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "u
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_read",
-           "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals"]
+           "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals",
+           "swe_ens_create", "swe_ens_destroy", "swe_ens_size", "swe_ens_layout", "swe_ens_rhs",
+           "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches"]
 
 
 class Params(ctypes.Structure):
@@ -29,6 +31,13 @@ class Params(ctypes.Structure):
                 ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
                 ("limiter", ctypes.c_int), ("h_tol", ctypes.c_double), ("rk", ctypes.c_int),
                 ("cfl", ctypes.c_double)]
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("K", ctypes.c_int), ("x", ctypes.POINTER(ctypes.c_double)),
+                ("y", ctypes.POINTER(ctypes.c_double)), ("b", ctypes.POINTER(ctypes.c_double)),
+                ("EToE", ctypes.POINTER(ctypes.c_int32)), ("EToF", ctypes.POINTER(ctypes.c_int32)),
+                ("flip", ctypes.POINTER(ctypes.c_int32))]
 
 
 class SweError(RuntimeError):
@@ -72,6 +81,20 @@ def lib():
     L.swe_info.argtypes = [vp, ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_int),
                            ctypes.POINTER(ctypes.c_int)]
     L.swe_integrals_noalloc.argtypes = [ctypes.c_int, ctypes.c_int, vp, vp, vp, ctypes.c_double, vp, vp]
+    i64p = ctypes.POINTER(ctypes.c_int64)
+    ip = ctypes.POINTER(ctypes.c_int)
+    L.swe_ens_create.argtypes = [ctypes.c_int, ctypes.POINTER(Instance), ctypes.c_double, ctypes.POINTER(Params),
+                                 ctypes.POINTER(vp)]
+    L.swe_ens_destroy.argtypes = [vp]
+    L.swe_ens_destroy.restype = None
+    L.swe_ens_size.argtypes = [vp, i64p, ip]
+    L.swe_ens_layout.argtypes = [vp, ctypes.c_int, i64p, i64p, ip, ip]
+    L.swe_ens_rhs.argtypes = [vp, vp, vp, vp]
+    L.swe_ens_max_dt.argtypes = [vp, vp, dp, dp, vp]
+    L.swe_ens_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, dp, vp]
+    L.swe_ens_integrals.argtypes = [vp, vp, dp, vp]
+    L.swe_ens_launches.argtypes = [vp]
+    L.swe_ens_launches.restype = ctypes.c_int64
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -214,3 +237,101 @@ class SweContext:
         N, K, nf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().swe_info(self._h, ctypes.byref(N), ctypes.byref(K), ctypes.byref(nf)))
         return N.value, K.value, nf.value
+
+
+class SweEnsemble:
+    """Many independent meshes of mixed degree advanced together
+    (swe_ens_create). State: one flat float64 CUDA tensor of `size` doubles;
+    `view(W, i)` is instance i's (3, K, n, n) view into it."""
+
+    def __init__(self, problems, g=9.81, flux=1, av=False, eps0=0.0, sigma_min=math.nan,
+                 sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("swedg needs a CUDA device; there is no CPU path")
+        L = lib()
+        self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
+                             int(limiter), float(h_tol), int(rk), float(cfl))
+        self.ninst = len(problems)
+        keep = []
+        arr = (Instance * self.ninst)()
+        d = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+        i32 = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_int32))
+        for i, p in enumerate(problems):
+            x, y, b = (np.ascontiguousarray(a, dtype=np.float64) for a in (p.x, p.y, p.b))
+            E, F, fl = (np.ascontiguousarray(a, dtype=np.int32) for a in (p.EToE, p.EToF, p.flip))
+            keep += [x, y, b, E, F, fl]
+            arr[i] = Instance(int(p.N), int(p.K), d(x), d(y), d(b), i32(E), i32(F), i32(fl))
+        h = ctypes.c_void_p()
+        _check(L.swe_ens_create(self.ninst, arr, float(g), ctypes.byref(self.params), ctypes.byref(h)))
+        self._h = h
+        tot, ng = ctypes.c_int64(), ctypes.c_int()
+        _check(L.swe_ens_size(h, ctypes.byref(tot), ctypes.byref(ng)))
+        self.size, self.ngroups = tot.value, ng.value
+        self.layout = []
+        for i in range(self.ninst):
+            off, st, N, K = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_int(), ctypes.c_int()
+            _check(L.swe_ens_layout(h, i, ctypes.byref(off), ctypes.byref(st), ctypes.byref(N), ctypes.byref(K)))
+            self.layout.append((off.value, st.value, N.value, K.value))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value and _lib is not None:
+            _lib.swe_ens_destroy(self._h)
+        self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def empty(self):
+        import torch
+        return torch.zeros(self.size, dtype=torch.float64, device="cuda")
+
+    def view(self, W, i):
+        """Instance i's (3, K, n, n) strided view of ensemble state W."""
+        off, st, N, K = self.layout[i]
+        n = N + 1
+        return W.as_strided((3, K, n, n), (st, n * n, n, 1), off)
+
+    def pack(self, states, W=None):
+        """Ensemble state from per-instance (3, K, n, n) arrays or tensors."""
+        import torch
+        W = self.empty() if W is None else W
+        for i, s in enumerate(states):
+            t = s if isinstance(s, torch.Tensor) else torch.from_numpy(np.ascontiguousarray(s))
+            self.view(W, i).copy_(t)
+        return W
+
+    def _state(self, W):
+        import torch
+        if not (isinstance(W, torch.Tensor) and W.is_cuda and W.dtype == torch.float64 and W.is_contiguous()
+                and W.numel() == self.size):
+            raise ValueError(f"ensemble state must be a contiguous float64 CUDA tensor of {self.size} values")
+        return ctypes.c_void_p(W.data_ptr())
+
+    def rhs(self, W, R=None, stream=None):
+        import torch
+        if R is None:
+            R = torch.zeros_like(W)
+        _check(lib().swe_ens_rhs(self._h, self._state(W), self._state(R), _stream(stream)))
+        return R
+
+    def max_dt(self, W, stream=None):
+        dc = (ctypes.c_double * self.ninst)()
+        dp = (ctypes.c_double * self.ninst)()
+        _check(lib().swe_ens_max_dt(self._h, self._state(W), dc, dp, _stream(stream)))
+        return np.array(dc[:]), np.array(dp[:])
+
+    def step(self, W, dt=0.0, nsteps=1, stream=None, raise_on_error=True):
+        dl = (ctypes.c_double * self.ninst)()
+        rc = lib().swe_ens_step(self._h, self._state(W), float(dt), int(nsteps), dl, _stream(stream))
+        if raise_on_error:
+            _check(rc)
+        return rc, np.array(dl[:])
+
+    def integrals(self, W, stream=None):
+        out = (ctypes.c_double * (4 * self.ninst))()
+        _check(lib().swe_ens_integrals(self._h, self._state(W), out, _stream(stream)))
+        return np.array(out[:]).reshape(self.ninst, 4)
+
+    def launches(self):
+        return int(lib().swe_ens_launches(self._h))
