@@ -28,6 +28,14 @@
  *  - Time step: dt_CFL = CFL * 2/(N+1) * min_nodes J/(lambda_xi + lambda_eta).
  *  - u = hu/h for h > 0, else 0; c = sqrt(g max(h,0)); {c} = (c- + c+)/2.
  *  - The limiter and the h_tol momentum cut act after every RK stage.
+ *  - Standard volume term (Eq. VolInt, second line; the paper states only the
+ *    volume integral of the standard DGSEM): D applied to the nodal
+ *    contravariant fluxes F~ = y_eta f - x_eta g, G~ = -y_xi f + x_xi g of
+ *    the physical fluxes, the same interface flux and lift as the split form
+ *    in strong form (F* - F~_own at the face nodes), and the non-split source
+ *    -g h J b_x, -g h J b_y with J b_x = y_eta b_xi - y_xi b_eta,
+ *    J b_y = -x_eta b_xi + x_xi b_eta (the continuous limit of the split
+ *    source).
  */
 #include "orc.h"
 
@@ -55,6 +63,7 @@ struct orc_mesh {
     double *x, *y, *b;
     double *x_xi, *x_eta, *y_xi, *y_eta, *J;
     double *beta_x, *beta_y;
+    double *jbx, *jby;      /* J b_x, J b_y of the standard-form source */
     int *EToE, *EToF, *flip;
     double *eps;
     /* work arrays */
@@ -260,7 +269,7 @@ static double deta(const orc_mesh* m, const double* f, int k, int i, int j) {
 void orc_destroy(orc_mesh* m) {
     if (!m) return;
     double* arrs[] = {m->x, m->y, m->b, m->x_xi, m->x_eta, m->y_xi, m->y_eta, m->J,
-                      m->beta_x, m->beta_y, m->eps, m->u, m->v, m->Fstar, m->Ustar,
+                      m->beta_x, m->beta_y, m->jbx, m->jby, m->eps, m->u, m->v, m->Fstar, m->Ustar,
                       m->grad, m->Fvstar};
     for (size_t a = 0; a < sizeof(arrs) / sizeof(arrs[0]); ++a) free(arrs[a]);
     free(m->EToE);
@@ -322,6 +331,7 @@ int orc_create(int N, int K, const double* x, const double* y, const int* EToE,
     m->x_xi = dalloc(nn); m->x_eta = dalloc(nn); m->y_xi = dalloc(nn); m->y_eta = dalloc(nn);
     m->J = dalloc(nn);
     m->beta_x = dalloc(nn); m->beta_y = dalloc(nn);
+    m->jbx = dalloc(nn); m->jby = dalloc(nn);
     m->eps = dalloc(K);
     m->u = dalloc(nn); m->v = dalloc(nn);
     m->Fstar = dalloc((size_t)K * NF * n * 3);
@@ -360,6 +370,8 @@ int orc_create(int N, int K, const double* x, const double* y, const int* EToE,
                               - m->y_xi[id] * beta - deta(m, tmp2, k, i, j);
                 m->beta_y[id] = m->x_eta[id] * bxi + dxi(m, tmp3, k, i, j)
                               - m->x_xi[id] * beta - deta(m, tmp4, k, i, j);
+                m->jbx[id] = m->y_eta[id] * bxi - m->y_xi[id] * beta;
+                m->jby[id] = -m->x_eta[id] * bxi + m->x_xi[id] * beta;
             }
     free(tmp1); free(tmp2); free(tmp3); free(tmp4);
     *out = m;
@@ -383,6 +395,17 @@ int orc_geometry(const orc_mesh* m, double* x_xi, double* x_eta, double* y_xi, d
 /* ------------------------------------------------------------------ */
 
 static double velocity(double h, double hu) { return h > 0.0 ? hu / h : 0.0; }
+
+/* Physical fluxes f, g of the shallow water equations (Sec. 2). */
+static void physical_flux(double g, const double* W, double* f, double* gf) {
+    double h = W[0], u = velocity(h, W[1]), v = velocity(h, W[2]);
+    f[0] = W[1];
+    f[1] = W[1] * u + 0.5 * g * h * h;
+    f[2] = W[1] * v;
+    gf[0] = W[2];
+    gf[1] = W[2] * u;
+    gf[2] = W[2] * v + 0.5 * g * h * h;
+}
 
 /* Entropy-conservative, well-balanced two-point volume fluxes F#, G#
  * (Eq. volumeFluxes). */
@@ -644,6 +667,39 @@ int orc_av_fields(orc_mesh* m, const double* W, double* eps, double* grads) {
     return ORC_OK;
 }
 
+/* Standard volume term of Eq. VolInt (second line) at node (i, j) of
+ * element k in strong form: D applied to the nodal contravariant fluxes and,
+ * at face nodes, the lift (F* - F~_own)/omega in the contravariant
+ * direction. */
+static void standard_volume(const orc_mesh* m, const double* W, int k, int i, int j, double* Lxi,
+                            double* Leta) {
+    int n = m->n, N = m->N;
+    double g = m->g;
+    for (int q = 0; q < n; ++q) {
+        double Wq[3], f[3], gf[3];
+        size_t iq = nid(m, k, q, j);
+        state_at(m, W, iq, Wq);
+        physical_flux(g, Wq, f, gf);
+        for (int c = 0; c < 3; ++c) Lxi[c] += m->D[i][q] * (m->y_eta[iq] * f[c] - m->x_eta[iq] * gf[c]);
+        size_t jq = nid(m, k, i, q);
+        state_at(m, W, jq, Wq);
+        physical_flux(g, Wq, f, gf);
+        for (int c = 0; c < 3; ++c) Leta[c] += m->D[j][q] * (-m->y_xi[jq] * f[c] + m->x_xi[jq] * gf[c]);
+    }
+    size_t id = nid(m, k, i, j);
+    double Wo[3], f[3], gf[3];
+    state_at(m, W, id, Wo);
+    physical_flux(g, Wo, f, gf);
+    for (int c = 0; c < 3; ++c) {
+        double Ft = m->y_eta[id] * f[c] - m->x_eta[id] * gf[c];
+        double Gt = -m->y_xi[id] * f[c] + m->x_xi[id] * gf[c];
+        if (i == N) Lxi[c] += (contravariant_star(m, m->Fstar, 3, k, 1, j, c) - Ft) / m->w[N];
+        if (i == 0) Lxi[c] -= (contravariant_star(m, m->Fstar, 3, k, 3, j, c) - Ft) / m->w[0];
+        if (j == N) Leta[c] += (contravariant_star(m, m->Fstar, 3, k, 2, i, c) - Gt) / m->w[N];
+        if (j == 0) Leta[c] -= (contravariant_star(m, m->Fstar, 3, k, 0, i, c) - Gt) / m->w[0];
+    }
+}
+
 int orc_rhs(orc_mesh* m, const double* W, double* R) {
     if (!m || !W || !R) return ORC_ERR_ARG;
     int n = m->n, N = m->N, K = m->K;
@@ -664,6 +720,13 @@ int orc_rhs(orc_mesh* m, const double* W, double* R) {
                 size_t id = nid(m, k, i, j);
                 double Wij[3], Lxi[3] = {0, 0, 0}, Leta[3] = {0, 0, 0};
                 state_at(m, W, id, Wij);
+                double S[3];
+                if (m->p.volume == 1) {
+                    standard_volume(m, W, k, i, j, Lxi, Leta);
+                    S[0] = 0.0;
+                    S[1] = -g * Wij[0] * m->jbx[id];
+                    S[2] = -g * Wij[0] * m->jby[id];
+                } else {
                 /* volume term of Eq. fluxDiffFormF with the fluxes of Eq. Fmij */
                 for (int q = 0; q < n; ++q) {
                     size_t iq = nid(m, k, q, j);
@@ -693,7 +756,10 @@ int orc_rhs(orc_mesh* m, const double* W, double* R) {
                     if (j == 0) Leta[c] -= contravariant_star(m, m->Fstar, 3, k, 0, i, c) / m->w[0];
                 }
                 /* source term (Eq. SourceDisc, reading in the header) */
-                double S[3] = {0.0, -0.5 * g * Wij[0] * m->beta_x[id], 0.5 * g * Wij[0] * m->beta_y[id]};
+                S[0] = 0.0;
+                S[1] = -0.5 * g * Wij[0] * m->beta_x[id];
+                S[2] = 0.5 * g * Wij[0] * m->beta_y[id];
+                }
                 /* viscous terms (Eq. ViscTermsDisc) */
                 double Lv[3] = {0.0, 0.0, 0.0};
                 if (m->p.av) {

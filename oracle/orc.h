@@ -43,6 +43,9 @@ typedef struct {
     double h_tol;     /* NaN: 1e-4 (Sec. 6.1) */
     int rk;           /* 0: LSRK4(5) (Carpenter-Kennedy 2N-storage), 1: SSPRK3 (Eq. RKSSP) */
     double cfl;       /* CFL number of the time-step rule */
+    int volume;       /* 0: split-form volume term (Eq. fluxDiffFormF with Eq. Fmij),
+                         1: standard volume term (Eq. VolInt, second line) with the
+                         non-split source -g h J grad b (reading in orc.c) */
 } orc_params;
 
 typedef struct orc_mesh orc_mesh;

@@ -189,6 +189,61 @@ def test_viscous_consistency_order(N):
 
 
 # ---------------------------------------------------------------------------
+# Standard volume term (Eq. VolInt, second line)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_standard_free_stream(N):
+    """Constant state, flat bottom, curved periodic mesh: the metric
+    identities make D (y_eta) - D (y_xi) vanish, so R = 0."""
+    p = I.random_smooth(N=N, K1=3, seed=4, rotate_seed=12, flat=True)
+    p.W = np.stack([np.ones_like(p.b), 0.3 * np.ones_like(p.b), -0.2 * np.ones_like(p.b)])
+    for flux in (0, 1):
+        R = O.Oracle(p, flux=flux, volume=1).rhs(p.W)
+        assert np.abs(R).max() < 1e-13 * term_scale(p)
+
+
+@pytest.mark.parametrize("N", [2, 3, 4])
+def test_standard_consistency_order(N):
+    """Manufactured smooth state with bottom topography: the standard form
+    converges to the exact W_t at order N or better."""
+    errs = []
+    for K1 in (4, 8, 16):
+        pm, Wt, _ = _manufactured(N, K1)
+        R = O.Oracle(pm, flux=1, volume=1).rhs(pm.W)
+        errs.append(np.abs(R - Wt).max())
+    rate = math.log(errs[-2] / errs[-1], 2)
+    assert rate > N - 0.5, (errs, rate)
+
+
+@pytest.mark.parametrize("flux", [0, 1])
+@pytest.mark.parametrize("N", [2, 3, 6])
+def test_standard_mass_conservation(flux, N):
+    """Discontinuous state: the interface lift (F* - F~_own) makes the
+    strong form conservative; a dropped or mis-signed lift breaks it."""
+    p = I.random_rough(N=N, K1=3, seed=N + 20, rotate_seed=N)
+    R = O.Oracle(p, flux=flux, av=True, eps0=0.05, volume=1).rhs(p.W)
+    tot = weighted(p, np.abs(R[0]))
+    assert abs(weighted(p, R[0])) < 1e-14 * tot
+
+
+def test_standard_differs_from_split_only_by_discretisation():
+    """On a smooth state both volume forms approximate the same W_t: their
+    difference shrinks with the mesh, while on a rough state it is O(1)."""
+    d = []
+    for K1 in (4, 8):
+        pm, _, _ = _manufactured(3, K1)
+        a = O.Oracle(pm, flux=1, volume=0).rhs(pm.W)
+        b = O.Oracle(pm, flux=1, volume=1).rhs(pm.W)
+        d.append(np.abs(a - b).max())
+    assert d[1] < d[0] / 4
+    p = I.random_rough(N=3, K1=3, seed=5)
+    a = O.Oracle(p, flux=1, volume=0).rhs(p.W)
+    b = O.Oracle(p, flux=1, volume=1).rhs(p.W)
+    assert np.abs(a - b).max() > 1e-3 * np.abs(a).max()
+
+
+# ---------------------------------------------------------------------------
 # Indicator (App. A)
 # ---------------------------------------------------------------------------
 
