@@ -138,7 +138,7 @@ def volume_traffic(N, nodes):
     on a smaller case of the same kernel and scaled by the node count), or
     None when the kernel source changed since the counters were taken."""
     import hashlib
-    src = os.path.join(ROOT, "paper_1804_02221_gb300", "csrc", "k_volume.cu")
+    src = os.path.join(ROOT, "paper_1804_02221_gb300", "csrc", "k_volume.cuh")
     summ = os.path.join(ROOT, "profiles", "volume_kernel_dam_break_N7.txt")
     if not os.path.exists(summ):
         return None
@@ -316,6 +316,14 @@ def ensemble_bench(args):
     ens.rhs(W0, R)
     ms_rhs_ens = timed(lambda: [ens.rhs(W0, R) for _ in range(5)]) / 5
 
+    groups_default = ens.groups()
+    groups_tuned = ens.autotune(W0)
+    W.copy_(W0)
+    ens.step(W, 0.0, 1)
+    W.copy_(W0)
+    ms_tuned = timed(lambda: ens.step(W, 0.0, args.steps)) / args.steps
+    same_tuned = torch.equal(W, Wens)
+
     ctxs = [swedg.SweContext.from_problem(p, **kw) for p in probs]
     Ws = [torch.from_numpy(p.W).cuda() for p in probs]
     for c, w in zip(ctxs, Ws):
@@ -339,7 +347,11 @@ def ensemble_bench(args):
                     "rhs_node_updates_per_s": nodes / (ms_rhs_ens * 1e-3)},
         "plain": {"value": rate(ms_plain), "ms_per_step": ms_plain, "gpu_launches": launches_plain,
                   "rhs_node_updates_per_s": nodes / (ms_rhs_plain * 1e-3)},
-        "speedup": ms_plain / ms_ens, "bitwise_equal": same,
+        "batched_autotuned": {"value": rate(ms_tuned), "ms_per_step": ms_tuned, "bitwise_equal": same_tuned,
+                              "groups": [{"N": g[0], "members": g[1], "volume_threads_per_block": g[2],
+                                          "update_warps_per_block": g[3]} for g in groups_tuned],
+                              "default_groups": [list(g) for g in groups_default]},
+        "speedup": ms_plain / ms_ens, "speedup_autotuned": ms_plain / ms_tuned, "bitwise_equal": same,
         "setup_s": {"inputs": t_gen, "create": t_create},
         "config": {"workload": f"uneven ensemble: {len(probs)} members, 16x16..96x96 curved periodic quads, "
                                "N in {3,5,7}, seeded 8-Gaussian bathymetry + Gaussian hump, ES+AV(eps0=0.01)"
@@ -390,6 +402,8 @@ def main():
     def one_step(Wd):
         ctx.step(Wd, 0.0, 1)
         ctx.integrals(Wd)  # mass, momenta and entropy, read back to the host
+
+    shapes = ctx.autotune(W0)  # launch shapes only: results are bitwise the same
 
     for _ in range(args.warmup):
         W.copy_(W0)
@@ -483,6 +497,7 @@ def main():
         "clocks": clk,
         "kernels": kernels,
         "rhs_only_node_updates_per_s": rhs_rates,
+        "launch_shapes": {"volume_threads_per_block": shapes[0], "update_warps_per_block": shapes[1]},
         "scalar_updates_per_s": 3 * value,
     }
     if not args.no_cpu_baseline and ws == 1:

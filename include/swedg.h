@@ -146,6 +146,20 @@ int swe_timing(swe_ctx* ctx, int on);
 int swe_timing_read(swe_ctx* ctx, int which, double* ms, int64_t* launches);
 int64_t swe_launches(const swe_ctx* ctx);
 
+/* Launch shapes (a performance choice only: every shape evaluates every
+ * element with the same instructions in the same order, so results are
+ * bitwise identical). The volume kernel runs blocks of vol_threads/(N+1)
+ * elements, one thread per element line (vol_threads 64, 128 or 256; a
+ * shape whose shared-memory staging exceeds 227 KB at this degree is
+ * rejected); the stage update runs one warp per element in blocks of
+ * upd_warps warps (2, 4 or 8). Defaults 128 and 4.
+ * swe_autotune times each shape on device state W (writing only the
+ * context's scratch buffers) and keeps the fastest; synchronises `stream`.
+ * swe_set_tuning returns SWE_ERR_ARG for a shape not listed above. */
+int swe_autotune(swe_ctx* ctx, const double* W, void* stream);
+int swe_get_tuning(const swe_ctx* ctx, int* vol_threads, int* upd_warps);
+int swe_set_tuning(swe_ctx* ctx, int vol_threads, int upd_warps);
+
 /* Sizes of a context: N, K and the number of unique faces. */
 int swe_info(const swe_ctx* ctx, int* N, int* K, int* nfaces);
 
@@ -246,6 +260,13 @@ int swe_ens_integrals(swe_ens* ens, const double* W, double* out, void* stream);
 
 /* Kernels launched so far (graph replays count their kernels). */
 int64_t swe_ens_launches(const swe_ens* ens);
+
+/* swe_autotune for every degree group on its part of ensemble state W (the
+ * step graph is captured again at the next swe_ens_step). Synchronises. */
+int swe_ens_autotune(swe_ens* ens, const double* W, void* stream);
+/* Degree group g (0 <= g < ngroups, increasing N): its N, member count and
+ * launch shapes. */
+int swe_ens_group(const swe_ens* ens, int g, int* N, int* members, int* vol_threads, int* upd_warps);
 
 /* Text of the last error on the calling thread ("" if none). */
 const char* swe_last_error(void);

@@ -483,6 +483,108 @@ extern "C" int swe_step(swe_ctx* c, double* W, double dt, int nsteps, double* dt
 }
 
 // ---------------------------------------------------------------------------
+// Launch-shape tuning
+// ---------------------------------------------------------------------------
+
+namespace swe {
+
+namespace {
+
+// Milliseconds of `reps` launches by fn on s, after one untimed launch.
+template <class F>
+float time_launches(cudaStream_t s, cudaEvent_t a, cudaEvent_t b, int reps, F fn) {
+    fn();
+    cudaEventRecord(a, s);
+    for (int r = 0; r < reps; ++r) fn();
+    cudaEventRecord(b, s);
+    if (cudaEventSynchronize(b) != cudaSuccess) return INFINITY;
+    float ms = INFINITY;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+}  // namespace
+
+int autotune_ctx(swe_ctx* c, const double* W, cudaStream_t s) {
+    cudaEvent_t a = nullptr, b = nullptr;
+    cudaError_t e = cudaEventCreate(&a);
+    if (e == cudaSuccess) e = cudaEventCreate(&b);
+    if (e != cudaSuccess) {
+        if (a) cudaEventDestroy(a);
+        return cuda_fail(e, "swe_autotune");
+    }
+    const bool timing = c->timing;
+    c->timing = false;
+    constexpr int kReps = 5;
+    // A switch away from the default shape must gain more than the noise.
+    constexpr float kMargin = 0.98f;
+    // The volume kernel needs the interface fluxes, viscosities and gradients
+    // of W: one right-hand side into the scratch buffer provides them.
+    rhs_chain(c, W, c->w.R, s, nullptr, false);
+    int best_v = 128;
+    c->vol_tpb = 128;
+    float t_best = time_launches(s, a, b, kReps, [&] { launch_volume(c, W, c->w.R, s, nullptr); });
+    for (int tpb : {64, 256}) {
+        if (!volume_shape_valid(c->m.N, tpb)) continue;
+        c->vol_tpb = tpb;
+        const float t = time_launches(s, a, b, kReps, [&] { launch_volume(c, W, c->w.R, s, nullptr); });
+        if (t < kMargin * t_best) {
+            t_best = t;
+            best_v = tpb;
+        }
+    }
+    c->vol_tpb = best_v;
+    // Stage update (2N-storage stage with a = b = 0: the register takes R, the
+    // state is only limited) on a scratch copy of W.
+    launch_copy(c, W, c->w.Wn, 3 * c->m.KN, s, nullptr);
+    int best_u = 4;
+    c->upd_wpb = 4;
+    auto upd = [&] { launch_update(c, 1, c->w.Wn, 0.0, 0.0, 0.0, nullptr, s, nullptr, false); };
+    t_best = time_launches(s, a, b, kReps, upd);
+    for (int wpb : {2, 8}) {
+        c->upd_wpb = wpb;
+        const float t = time_launches(s, a, b, kReps, upd);
+        if (t < kMargin * t_best) {
+            t_best = t;
+            best_u = wpb;
+        }
+    }
+    c->upd_wpb = best_u;
+    c->timing = timing;
+    e = cudaStreamSynchronize(s);
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (e == cudaSuccess) e = cudaGetLastError();
+    return e == cudaSuccess ? SWE_OK : cuda_fail(e, "swe_autotune");
+}
+
+}  // namespace swe
+
+extern "C" int swe_autotune(swe_ctx* c, const double* W, void* stream) {
+    if (!c || !W) return fail(SWE_ERR_ARG, "swe_autotune: NULL argument");
+    return swe::autotune_ctx(c, W, (cudaStream_t)stream);
+}
+
+extern "C" int swe_get_tuning(const swe_ctx* c, int* vol_threads, int* upd_warps) {
+    if (!c) return fail(SWE_ERR_ARG, "swe_get_tuning: NULL context");
+    if (vol_threads) *vol_threads = c->vol_tpb;
+    if (upd_warps) *upd_warps = c->upd_wpb;
+    return SWE_OK;
+}
+
+extern "C" int swe_set_tuning(swe_ctx* c, int vol_threads, int upd_warps) {
+    if (!c) return fail(SWE_ERR_ARG, "swe_set_tuning: NULL context");
+    if (!swe::volume_shape_valid(c->m.N, vol_threads))
+        return fail(SWE_ERR_ARG, "swe_set_tuning: volume threads per block must be 64, 128 or 256 "
+                                 "(and the shape must fit the shared memory at this degree)");
+    if (upd_warps != 2 && upd_warps != 4 && upd_warps != 8)
+        return fail(SWE_ERR_ARG, "swe_set_tuning: update warps per block must be 2, 4 or 8");
+    c->vol_tpb = vol_threads;
+    c->upd_wpb = upd_warps;
+    return SWE_OK;
+}
+
+// ---------------------------------------------------------------------------
 // Diagnostics, status, timing
 // ---------------------------------------------------------------------------
 

@@ -370,3 +370,32 @@ extern "C" int swe_ens_integrals(swe_ens* e, const double* W, double* out, void*
 }
 
 extern "C" int64_t swe_ens_launches(const swe_ens* e) { return e ? e->launches : 0; }
+
+extern "C" int swe_ens_autotune(swe_ens* e, const double* W, void* stream) {
+    if (int rc = check_ens(e, W)) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    const int64_t before = sum_launches(e);
+    for (size_t gi = 0; gi < e->groups.size(); ++gi)
+        if (int rc = swe::autotune_ctx(e->groups[gi], W + e->goff[gi], s)) return rc;
+    e->launches += sum_launches(e) - before;
+    // The captured step holds the old shapes: capture again at the next step.
+    if (e->exec) {
+        cudaError_t err = cudaDeviceSynchronize();
+        if (err != cudaSuccess) return ecuda(err, "swe_ens_autotune");
+        cudaGraphExecDestroy(e->exec);
+        e->exec = nullptr;
+    }
+    return SWE_OK;
+}
+
+extern "C" int swe_ens_group(const swe_ens* e, int group, int* N, int* members, int* vol_threads,
+                             int* upd_warps) {
+    if (!e) return efail(SWE_ERR_ARG, "swe_ens_group: NULL ensemble");
+    if (group < 0 || group >= (int)e->groups.size()) return efail(SWE_ERR_ARG, "swe_ens_group: group out of range");
+    const swe_ctx* c = e->groups[group];
+    if (N) *N = c->m.N;
+    if (members) *members = e->gcount[group];
+    if (vol_threads) *vol_threads = c->vol_tpb;
+    if (upd_warps) *upd_warps = c->upd_wpb;
+    return SWE_OK;
+}

@@ -135,7 +135,7 @@ struct UpdArgs {
     const int* stop;
 };
 
-constexpr int UPD_WPB = 4;  // warps (elements) per block
+constexpr int UPD_MAX_WPB = 8;  // warps (elements) per block: 2, 4 (default) or 8 (swe_autotune)
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -273,12 +273,13 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, in
     }
 }
 
-// One warp per element, blocks looping over the elements (persistent grid).
+// One warp per element, blocks of blockDim.x/32 elements looping over the
+// elements.
 template <int N, int MODE>
-__global__ void __launch_bounds__(32 * UPD_WPB) k_update(UpdArgs a) {
+__global__ void __launch_bounds__(32 * UPD_MAX_WPB) k_update(UpdArgs a) {
     if (stopped(a.stop)) return;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    for (long long k = (long long)blockIdx.x * UPD_WPB + wid; k < a.m.K; k += (long long)gridDim.x * UPD_WPB)
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (long long k = (long long)blockIdx.x * wpb + wid; k < a.m.K; k += (long long)gridDim.x * wpb)
         update_element<N, MODE>(a, k, lane);
 }
 
@@ -455,11 +456,12 @@ __global__ void k_reduce_inst(DeviceMesh m, const double* __restrict__ W, const 
 
 template <int N>
 void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
-    const int blocks = persistent_grid(c, UPD_WPB);
+    const int wpb = c->upd_wpb;
+    const int blocks = persistent_grid(c, wpb);
     Timed tm(c, KC_UPDATE, s);
-    if (mode == 0) k_update<N, 0><<<blocks, 32 * UPD_WPB, 0, s>>>(a);
-    else if (mode == 1) k_update<N, 1><<<blocks, 32 * UPD_WPB, 0, s>>>(a);
-    else k_update<N, 2><<<blocks, 32 * UPD_WPB, 0, s>>>(a);
+    if (mode == 0) k_update<N, 0><<<blocks, 32 * wpb, 0, s>>>(a);
+    else if (mode == 1) k_update<N, 1><<<blocks, 32 * wpb, 0, s>>>(a);
+    else k_update<N, 2><<<blocks, 32 * wpb, 0, s>>>(a);
 }
 
 template <int N>

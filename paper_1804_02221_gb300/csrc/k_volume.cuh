@@ -1,0 +1,332 @@
+// Volume kernel, the template of all launch shapes: split-form flux
+// differencing (Eq. fluxDiffFormF with the curvilinear two-point fluxes of
+// Eq. Fmij and Eq. volumeFluxes), the
+// interface-flux lift of Eq. fluxDiffFormF, the BR1 viscous divergence of
+// Eq. ViscTermsDisc, the well-balanced source of Eq. SourceDisc, and the
+// scaling R = -(L - S - L^v)/J of Eq. CurvilinearECDGSEMviscous.
+//
+// Design (FP64-ALU bound on GB300):
+//  * The two-point flux is symmetric, so each node pair (i, q) of a line is
+//    evaluated once. The accumulators hold w_i w_j L (the quadrature weight
+//    of the node times L); by the SBP property w_q D_qi = -w_i D_iq, so the
+//    partner node receives exactly the negative of the node's contribution,
+//    and the diagonal of D~ = 2D + S vanishes for LGL nodes.
+//  * The static per-pair factor w_i w_j D_iq / 4 (a_i + a_q) (a the
+//    contravariant vector of the line direction: (y_eta, -x_eta) along xi,
+//    (-y_xi, x_xi) along eta) is precomputed on the host, so one pair costs
+//      Q  = (hu_i+hu_q) Sx + (hv_i+hv_q) Sy,   P = 2g h_i h_q,
+//      X2 = (u_i+u_q) Q + P Sx,                X3 = (v_i+v_q) Q + P Sy,
+//    contributions (2Q, X2, X3) to node i and their negatives to node q:
+//    17 FP64 instructions.
+//  * One thread per element line: it runs its xi-line, hands the results
+//    through shared memory, then runs the eta-line with the same index
+//    starting from them, and finishes the nodes of that column (interface
+//    lifts, viscous terms, source, scaling by -1/(w_i w_j J)) in registers.
+//    The loops are fully unrolled: all pair indices are compile-time.
+//  * Launch shapes: blocks of TPB/(N+1) elements (TPB = 64, 128, 256), one
+//    translation unit per shape; every shape computes every element with the
+//    same instructions in the same order, so the results are bitwise equal
+//    and the shape is a pure performance choice (swe_autotune).
+#pragma once
+#include "kcommon.cuh"
+
+namespace swe {
+namespace {
+
+// Shared-memory planes of the staged elements. After the eta pass, blocks
+// with viscous elements reuse the planes of hu, hv, u, v for the
+// contravariant viscous fluxes.
+enum { F_H, F_HU, F_HV, F_U, F_V, F_P, F_A1, F_A2, F_A3, F_COUNT };
+enum { F_FT2 = F_HU, F_FT3 = F_HV, F_GT2 = F_U, F_GT3 = F_V };
+
+struct VolArgs {
+    DeviceMesh m;
+    const double* W;
+    const double* uv;
+    const double* Fout;
+    const double* Fvt;
+    const double* Fvout;
+    const double* eps;
+    double* R;
+    const int* stop;
+};
+
+// Elements per block of the launch shape with (about) TPB threads.
+template <int N, int TPB>
+constexpr int vol_ne() {
+    return (TPB / (N + 1)) > 0 ? TPB / (N + 1) : 1;
+}
+
+template <int N, bool AV, int TPB>
+constexpr size_t vol_smem() {
+    return sizeof(double) *
+           ((size_t)F_COUNT * vol_ne<N, TPB>() * (N + 1) * (N + 1) + (AV ? (N + 1) * (N + 1) : 0));
+}
+
+// Shapes whose staging exceeds the 227 KB of shared memory a block may use
+// are not built (the 128-thread shape fits every degree).
+template <int N, bool AV, int TPB>
+constexpr bool vol_fits() {
+    return vol_smem<N, AV, TPB>() <= 227 * 1024;
+}
+
+template <int N>
+__host__ __device__ constexpr int pair_index(int i, int q) {
+    return i * (N + 1) - i * (i + 1) / 2 + (q - i - 1);
+}
+
+// All pairs of one line: nodes base + p*stride, p = 0..N; pair constants at
+// pmk[(2*pair + c) * (N+1)].
+template <int N, int BLK>
+__device__ __forceinline__ void pair_loop(const double* __restrict__ s, int base, int stride,
+                                          const double* __restrict__ pmk, double* A1, double* A2,
+                                          double* A3) {
+    constexpr int n = N + 1;
+    const double* sH = s + F_H * BLK;
+    const double* sHU = s + F_HU * BLK;
+    const double* sHV = s + F_HV * BLK;
+    const double* sU = s + F_U * BLK;
+    const double* sV = s + F_V * BLK;
+    const double* sP = s + F_P * BLK;
+#pragma unroll
+    for (int i = 0; i < n; ++i) {
+        const int ni = base + i * stride;
+        const double hu_i = sHU[ni], hv_i = sHV[ni], u_i = sU[ni], v_i = sV[ni], p_i = sP[ni];
+#pragma unroll
+        for (int q = i + 1; q < n; ++q) {
+            const int nq = base + q * stride;
+            const int pr = pair_index<N>(i, q);
+            const double sx = __ldg(pmk + (2 * pr) * n), sy = __ldg(pmk + (2 * pr + 1) * n);
+            const double Q = fma(hu_i + sHU[nq], sx, (hv_i + sHV[nq]) * sy);
+            const double P = p_i * sH[nq];
+            const double X2 = fma(u_i + sU[nq], Q, P * sx);
+            const double X3 = fma(v_i + sV[nq], Q, P * sy);
+            A1[i] = fma(2.0, Q, A1[i]);
+            A1[q] = fma(-2.0, Q, A1[q]);
+            A2[i] += X2;
+            A2[q] -= X2;
+            A3[i] += X3;
+            A3[q] -= X3;
+        }
+    }
+}
+
+template <int N, bool AV, int TPB>
+__global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1)) k_volume(VolArgs a) {
+    constexpr int n = N + 1, nn = n * n, NE = vol_ne<N, TPB>(), NT = NE * n, BLK = NE * nn;
+    constexpr int NP = N * (N + 1) / 2;
+    extern __shared__ double sm[];
+    if (stopped(a.stop)) return;
+    const DeviceMesh& m = a.m;
+    const int t = threadIdx.x;
+    const long long k0 = (long long)blockIdx.x * NE;
+    auto S = [&](int f) { return sm + f * BLK; };
+    double* sD = sm + F_COUNT * BLK;
+
+    // ---- stage the block's elements ---------------------------------------
+    const double g2 = 2.0 * m.g;
+    for (int idx = t; idx < BLK; idx += NT) {
+        const int e = idx / nn;
+        const long long k = k0 + e;
+        double h = 0, hu = 0, hv = 0, u = 0, v = 0;
+        if (k < m.K) {
+            const long long gid = k * nn + (idx - e * nn);
+            h = a.W[gid];
+            hu = a.W[m.KN + gid];
+            hv = a.W[2 * m.KN + gid];
+            u = a.uv[gid];
+            v = a.uv[m.KN + gid];
+        }
+        S(F_H)[idx] = h;
+        S(F_HU)[idx] = hu;
+        S(F_HV)[idx] = hv;
+        S(F_U)[idx] = u;
+        S(F_V)[idx] = v;
+        S(F_P)[idx] = g2 * h;
+    }
+    __syncthreads();
+
+    const int e = t / n, l = t - e * n;
+    const long long k = k0 + e;
+    const bool valid = k < m.K;
+    const double* pmx = m.pm + ((size_t)(valid ? k : 0) * 2 * NP * 2) * n + l;
+    const double* pme = pmx + (size_t)NP * 2 * n;
+    double A1[n], A2[n], A3[n];
+
+    // ---- xi-line j = l ----------------------------------------------------
+#pragma unroll
+    for (int p = 0; p < n; ++p) A1[p] = A2[p] = A3[p] = 0.0;
+    if (valid) pair_loop<N, BLK>(sm, e * nn + l * n, 1, pmx, A1, A2, A3);
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        S(F_A1)[e * nn + l * n + p] = A1[p];
+        S(F_A2)[e * nn + l * n + p] = A2[p];
+        S(F_A3)[e * nn + l * n + p] = A3[p];
+    }
+    __syncthreads();
+
+    // ---- eta-line i = l, starting from the xi results ----------------------
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        A1[p] = S(F_A1)[e * nn + p * n + l];
+        A2[p] = S(F_A2)[e * nn + p * n + l];
+        A3[p] = S(F_A3)[e * nn + p * n + l];
+    }
+    if (valid) pair_loop<N, BLK>(sm, e * nn + l, n, pme, A1, A2, A3);
+
+    // ---- viscous fluxes of the block's viscous elements --------------------
+    const double ek = (AV && valid) ? a.eps[k] : 0.0;
+    if (AV) {
+        const int any = __syncthreads_or(ek > 0.0);
+        if (any) {
+            for (int idx = t; idx < BLK; idx += NT) {
+                const int ee = idx / nn;
+                const long long kk = k0 + ee;
+                if (kk < m.K && a.eps[kk] > 0.0) {
+                    const long long gid = kk * nn + (idx - ee * nn);
+                    S(F_FT2)[idx] = a.Fvt[gid];
+                    S(F_FT3)[idx] = a.Fvt[m.KN + gid];
+                    S(F_GT2)[idx] = a.Fvt[2 * m.KN + gid];
+                    S(F_GT3)[idx] = a.Fvt[3 * m.KN + gid];
+                }
+            }
+            for (int idx = t; idx < nn; idx += NT) sD[idx] = Dm<N>(idx / n, idx % n);
+        }
+        __syncthreads();
+    }
+    if (!valid) return;
+
+    // ---- nodes (i = l, j = p): lifts, viscous terms, source, scaling --------
+    const int i = l;
+    const double wi = c_w[vec_offset(N) + i];
+    const long long KS = m.KS;
+    const long long side = k * 4 * n;
+    const int eb = e * nn;
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        const int j = p;
+        const double wj = wq<N>(j);
+        const long long gid = k * nn + j * n + i;
+        double a1 = A1[p], a2 = A2[p], a3 = A3[p];
+        // interface flux: w_i w_j (1/w_0) F_out = (tangential weight) F_out
+        auto lift = [&](int f, int pn, double wt) {
+            const long long sl = side + f * n + pn;
+            a1 = fma(wt, a.Fout[sl], a1);
+            a2 = fma(wt, a.Fout[KS + sl], a2);
+            a3 = fma(wt, a.Fout[2 * KS + sl], a3);
+        };
+        if (j == 0) lift(0, i, wi);
+        if (j == N) lift(2, i, wi);
+        if (i == N) lift(1, j, wj);
+        if (i == 0) lift(3, j, wj);
+        if (AV) {
+            const bool visc = ek > 0.0;
+            const int nd = eb + j * n + i;
+            if (visc) {
+                double L2 = 0.0, L3 = 0.0;
+#pragma unroll
+                for (int q = 0; q < n; ++q) {
+                    const double di = sD[i * n + q], dj = Dm<N>(j, q);
+                    L2 = fma(di, S(F_FT2)[eb + j * n + q], L2);
+                    L3 = fma(di, S(F_FT3)[eb + j * n + q], L3);
+                    L2 = fma(dj, S(F_GT2)[eb + q * n + i], L2);
+                    L3 = fma(dj, S(F_GT3)[eb + q * n + i], L3);
+                }
+                const double wij = wi * wj;
+                a2 = fma(-wij, L2, a2);
+                a3 = fma(-wij, L3, a3);
+            }
+            const double ft2 = visc ? S(F_FT2)[nd] : 0.0, ft3 = visc ? S(F_FT3)[nd] : 0.0;
+            const double gt2 = visc ? S(F_GT2)[nd] : 0.0, gt3 = visc ? S(F_GT3)[nd] : 0.0;
+            // viscous lift: -(tangential weight) (F^v*_out - own outward flux)
+            auto vlift = [&](int f, int pn, double wt, double own2, double own3) {
+                const long long sl = side + f * n + pn;
+                a2 = fma(-wt, a.Fvout[sl] - own2, a2);
+                a3 = fma(-wt, a.Fvout[KS + sl] - own3, a3);
+            };
+            if (j == 0) vlift(0, i, wi, -gt2, -gt3);
+            if (j == N) vlift(2, i, wi, gt2, gt3);
+            if (i == N) vlift(1, j, wj, ft2, ft3);
+            if (i == 0) vlift(3, j, wj, -ft2, -ft3);
+        }
+        const double f = m.fwJ[gid];
+        const double h = S(F_H)[eb + j * n + i];
+        a.R[gid] = f * a1;
+        a.R[m.KN + gid] = fma(h, m.srcx[gid], f * a2);
+        a.R[2 * m.KN + gid] = fma(h, m.srcy[gid], f * a3);
+    }
+}
+
+// Opt in to the kernel's shared memory once per process (before any stream
+// capture: contexts call it at creation).
+template <int N, bool AV, int TPB>
+void set_attr() {
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_volume<N, AV, TPB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)vol_smem<N, AV, TPB>());
+        attr = true;
+    }
+}
+
+template <int N, bool AV, int TPB>
+bool launch_n(swe_ctx* c, const VolArgs& a, cudaStream_t s) {
+    if constexpr (!vol_fits<N, AV, TPB>()) {
+        return false;
+    } else {
+        constexpr int NE = vol_ne<N, TPB>();
+        set_attr<N, AV, TPB>();
+        const int blocks = grid_for(c->m.K, NE);
+        Timed tm(c, KC_VOLUME, s);
+        k_volume<N, AV, TPB><<<blocks, NE * (N + 1), vol_smem<N, AV, TPB>(), s>>>(a);
+        return true;
+    }
+}
+
+template <int N, int TPB>
+bool prepare_n() {
+    if constexpr (vol_fits<N, true, TPB>()) set_attr<N, true, TPB>();
+    if constexpr (vol_fits<N, false, TPB>()) set_attr<N, false, TPB>();
+    return vol_fits<N, true, TPB>() && vol_fits<N, false, TPB>();
+}
+
+template <int TPB>
+bool prepare_shape(int N) {
+    switch (N) {
+        case 1: return prepare_n<1, TPB>(); case 2: return prepare_n<2, TPB>();
+        case 3: return prepare_n<3, TPB>(); case 4: return prepare_n<4, TPB>();
+        case 5: return prepare_n<5, TPB>(); case 6: return prepare_n<6, TPB>();
+        case 7: return prepare_n<7, TPB>(); case 8: return prepare_n<8, TPB>();
+        case 9: return prepare_n<9, TPB>(); case 10: return prepare_n<10, TPB>();
+        case 11: return prepare_n<11, TPB>(); case 12: return prepare_n<12, TPB>();
+        default: return false;
+    }
+}
+
+template <int TPB>
+bool launch_shape(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop) {
+    VolArgs a{c->m, W, c->w.uv, c->w.Fout, c->w.Fvt, c->w.Fvout, c->w.eps, R, stop};
+    const bool av = c->p.av != 0;
+#define SWE_VOL_CASE(NN) \
+    case NN: return av ? launch_n<NN, true, TPB>(c, a, s) : launch_n<NN, false, TPB>(c, a, s);
+    switch (c->m.N) {
+        SWE_VOL_CASE(1) SWE_VOL_CASE(2) SWE_VOL_CASE(3) SWE_VOL_CASE(4)
+        SWE_VOL_CASE(5) SWE_VOL_CASE(6) SWE_VOL_CASE(7) SWE_VOL_CASE(8)
+        SWE_VOL_CASE(9) SWE_VOL_CASE(10) SWE_VOL_CASE(11) SWE_VOL_CASE(12)
+        default: return false;
+    }
+#undef SWE_VOL_CASE
+}
+
+}  // namespace
+}  // namespace swe
+
+// Exported entry points of the translation unit of one launch shape.
+#define SWE_VOLUME_SHAPE(TPB)                                                                        \
+    namespace swe {                                                                                  \
+    void volume_init_##TPB() { upload_tables(); }                                                    \
+    bool volume_prepare_##TPB(int N) { return prepare_shape<TPB>(N); }                                 \
+    bool volume_launch_##TPB(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop) { \
+        return launch_shape<TPB>(c, W, R, s, stop);                                                  \
+    }                                                                                                \
+    }

@@ -1,0 +1,4 @@
+// Volume kernel, launch shape of 256 threads per block (k_volume.cuh).
+#include "k_volume.cuh"
+
+SWE_VOLUME_SHAPE(256)

@@ -135,6 +135,9 @@ struct swe_ctx {
     swe::Work w{};
     std::vector<void*> allocations;
     int64_t launches = 0;
+    // launch shapes (swe_autotune): volume threads per block, update warps per block
+    int vol_tpb = 128;
+    int upd_wpb = 4;
     // timing
     bool timing = false;
     std::vector<cudaEvent_t> ev;
@@ -152,6 +155,19 @@ void init_tables_av();
 // Per-process kernel attributes of the context's degree (called at creation,
 // so that later launches, also inside a stream capture, change no state).
 void prepare_volume(swe_ctx* c);
+// Volume-kernel launch shapes (threads per block 64, 128, 256; one
+// translation unit each). launch returns false if the shape does not fit the
+// degree (then nothing is launched); prepare returns whether it fits.
+void volume_init_64();
+void volume_init_128();
+void volume_init_256();
+bool volume_prepare_64(int N);
+bool volume_prepare_128(int N);
+bool volume_prepare_256(int N);
+bool volume_launch_64(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
+bool volume_launch_128(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
+bool volume_launch_256(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
+bool volume_shape_valid(int N, int tpb);
 
 void launch_prim(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
@@ -185,6 +201,10 @@ void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int
 // all those copies before any of the steps, so that a failure in one
 // context cannot stop another's copy).
 void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop, bool save = true);
+
+// Pick the fastest launch shapes of the volume kernel and the stage update
+// for this context on W (scratch buffers only); synchronises s.
+int autotune_ctx(swe_ctx* c, const double* W, cudaStream_t s);
 
 // Context construction (swe_create; ensembles pass an instance map and a
 // status word shared by their groups).

@@ -23,7 +23,8 @@ SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "s
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_read",
            "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals",
            "swe_ens_create", "swe_ens_destroy", "swe_ens_size", "swe_ens_layout", "swe_ens_rhs",
-           "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches"]
+           "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches", "swe_autotune",
+           "swe_get_tuning", "swe_set_tuning", "swe_ens_autotune", "swe_ens_group"]
 
 
 class Params(ctypes.Structure):
@@ -95,6 +96,11 @@ def lib():
     L.swe_ens_integrals.argtypes = [vp, vp, dp, vp]
     L.swe_ens_launches.argtypes = [vp]
     L.swe_ens_launches.restype = ctypes.c_int64
+    L.swe_autotune.argtypes = [vp, vp, vp]
+    L.swe_get_tuning.argtypes = [vp, ip, ip]
+    L.swe_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
+    L.swe_ens_autotune.argtypes = [vp, vp, vp]
+    L.swe_ens_group.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip]
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -233,6 +239,19 @@ class SweContext:
     def launches(self):
         return int(lib().swe_launches(self._h))
 
+    def autotune(self, W, stream=None):
+        """Time the launch shapes on W and keep the fastest; returns them."""
+        _check(lib().swe_autotune(self._h, self._state(W), _stream(stream)))
+        return self.tuning()
+
+    def tuning(self):
+        v, u = ctypes.c_int(), ctypes.c_int()
+        _check(lib().swe_get_tuning(self._h, ctypes.byref(v), ctypes.byref(u)))
+        return v.value, u.value
+
+    def set_tuning(self, vol_threads, upd_warps):
+        _check(lib().swe_set_tuning(self._h, int(vol_threads), int(upd_warps)))
+
     def info(self):
         N, K, nf = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
         _check(lib().swe_info(self._h, ctypes.byref(N), ctypes.byref(K), ctypes.byref(nf)))
@@ -335,3 +354,16 @@ class SweEnsemble:
 
     def launches(self):
         return int(lib().swe_ens_launches(self._h))
+
+    def autotune(self, W, stream=None):
+        _check(lib().swe_ens_autotune(self._h, self._state(W), _stream(stream)))
+        return self.groups()
+
+    def groups(self):
+        """[(N, members, volume threads per block, update warps per block)] per degree group."""
+        out = []
+        for g in range(self.ngroups):
+            v = [ctypes.c_int() for _ in range(4)]
+            _check(lib().swe_ens_group(self._h, g, *[ctypes.byref(x) for x in v]))
+            out.append(tuple(x.value for x in v))
+        return out
