@@ -119,6 +119,17 @@ static int is_owner(const orc_mesh* m, int k, int f) {
     return kk > k || (kk == k && ff > f);
 }
 
+static int is_wall(const orc_mesh* m, int k, int f) { return m->EToE[NF * k + f] < 0; }
+
+/* Solid wall: the mirror state of W (same h, normal velocity reversed about
+ * the unit normal (nx, ny), tangential velocity kept). */
+static void wall_state(const double* W, double nx, double ny, double* Wg) {
+    double mn = W[1] * nx + W[2] * ny;
+    Wg[0] = W[0];
+    Wg[1] = W[1] - 2.0 * mn * nx;
+    Wg[2] = W[2] - 2.0 * mn * ny;
+}
+
 static int neighbour_node(const orc_mesh* m, int k, int f, int p) {
     return m->flip[NF * k + f] ? m->N - p : p;
 }
@@ -317,10 +328,11 @@ int orc_create(int N, int K, const double* x, const double* y, const int* EToE,
     memcpy(m->EToE, EToE, sizeof(int) * NF * K);
     memcpy(m->EToF, EToF, sizeof(int) * NF * K);
     memcpy(m->flip, flip, sizeof(int) * NF * K);
-    /* connectivity must be reciprocal; boundary faces are not supported */
+    /* connectivity must be reciprocal; EToE = -1 marks a solid wall */
     for (int k = 0; k < K; ++k)
         for (int f = 0; f < NF; ++f) {
             int kk = EToE[NF * k + f], ff = EToF[NF * k + f];
+            if (kk == -1) continue;
             if (kk < 0 || kk >= K || ff < 0 || ff >= NF || (kk == k && ff == f) ||
                 EToE[NF * kk + ff] != k || EToF[NF * kk + ff] != f ||
                 flip[NF * kk + ff] != flip[NF * k + f]) {
@@ -546,6 +558,25 @@ static void interface_terms(orc_mesh* m, const double* W) {
     int n = m->n;
     for (int k = 0; k < m->K; ++k)
         for (int f = 0; f < NF; ++f) {
+            if (is_wall(m, k, f)) {
+                /* the numerical flux against the mirror state; BR1 takes the
+                   own value as U* (no gradient lift at walls) */
+                for (int p = 0; p < n; ++p) {
+                    int i, j;
+                    face_node(m->N, f, p, &i, &j);
+                    size_t im = nid(m, k, i, j);
+                    double Wm[3], Wg[3], F[3], nx, ny;
+                    state_at(m, W, im, Wm);
+                    outward_normal(m, k, f, p, &nx, &ny);
+                    double Jsurf = sqrt(nx * nx + ny * ny);
+                    wall_state(Wm, nx / Jsurf, ny / Jsurf, Wg);
+                    orc_surface_flux(m->g, m->p.flux, Wm, Wg, m->b[im], m->b[im], nx / Jsurf, ny / Jsurf, F);
+                    for (int c = 0; c < 3; ++c) m->Fstar[sid(m, k, f, p) * 3 + c] = Jsurf * F[c];
+                    m->Ustar[sid(m, k, f, p) * 2 + 0] = m->u[im];
+                    m->Ustar[sid(m, k, f, p) * 2 + 1] = m->v[im];
+                }
+                continue;
+            }
             if (!is_owner(m, k, f)) continue;
             int kk = m->EToE[NF * k + f], ff = m->EToF[NF * k + f];
             for (int p = 0; p < n; ++p) {
@@ -635,6 +666,12 @@ static void viscous_interface(orc_mesh* m, const double* W) {
     int n = m->n;
     for (int k = 0; k < m->K; ++k)
         for (int f = 0; f < NF; ++f) {
+            if (is_wall(m, k, f)) {
+                /* no viscous flux through a wall */
+                for (int p = 0; p < n; ++p)
+                    for (int c = 0; c < 2; ++c) m->Fvstar[sid(m, k, f, p) * 2 + c] = 0.0;
+                continue;
+            }
             if (!is_owner(m, k, f)) continue;
             int kk = m->EToE[NF * k + f], ff = m->EToF[NF * k + f];
             for (int p = 0; p < n; ++p) {
@@ -869,11 +906,16 @@ int orc_max_dt(orc_mesh* m, const double* W, double* dt_cfl, double* dt_pos) {
         for (int k = 0; k < K; ++k)
             for (int f = 0; f < NF; ++f) {
                 int kk = m->EToE[NF * k + f], ff = m->EToF[NF * k + f];
+                int wall = kk < 0;
                 for (int p = 0; p < n; ++p) {
-                    int q = neighbour_node(m, k, f, p), i, j, ii, jj;
+                    int i, j;
                     face_node(N, f, p, &i, &j);
-                    face_node(N, ff, q, &ii, &jj);
-                    size_t im = nid(m, k, i, j), ip = nid(m, kk, ii, jj);
+                    size_t im = nid(m, k, i, j), ip = im;
+                    if (!wall) {
+                        int q = neighbour_node(m, k, f, p), ii, jj;
+                        face_node(N, ff, q, &ii, &jj);
+                        ip = nid(m, kk, ii, jj);
+                    }
                     double nx, ny;
                     outward_normal(m, k, f, p, &nx, &ny);
                     double Jsurf = sqrt(nx * nx + ny * ny);
@@ -881,7 +923,8 @@ int orc_max_dt(orc_mesh* m, const double* W, double* dt_cfl, double* dt_pos) {
                     ny /= Jsurf;
                     double hm = W[im], hp = W[ip];
                     double utm = nx * velocity(hm, W[nn + im]) + ny * velocity(hm, W[2 * nn + im]);
-                    double utp = nx * velocity(hp, W[nn + ip]) + ny * velocity(hp, W[2 * nn + ip]);
+                    /* the mirror state at a wall reverses the normal velocity */
+                    double utp = wall ? -utm : nx * velocity(hp, W[nn + ip]) + ny * velocity(hp, W[2 * nn + ip]);
                     double ut_avg = 0.5 * (utm + utp);
                     double c_avg = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
                     double A = fabs(ut_avg + c_avg) + fabs(ut_avg - c_avg);

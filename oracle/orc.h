@@ -16,7 +16,9 @@
  * (h, hu, hv). Element faces: 0: eta=-1 (j=0), 1: xi=+1 (i=N), 2: eta=+1
  * (j=N), 3: xi=-1 (i=0); face node p runs along increasing xi (faces 0,2) or
  * eta (faces 1,3). Node p of face (k,f) meets node (flip ? N-p : p) of face
- * (EToE[k][f], EToF[k][f]).
+ * (EToE[k][f], EToF[k][f]); EToE[k][f] = -1 makes the face a solid wall
+ * (mirror state for the interface flux and the time step, U* = own value
+ * and no viscous flux for BR1).
  */
 #ifndef ORC_H
 #define ORC_H

@@ -97,7 +97,7 @@ def _canonical_face_of(N: int, i: np.ndarray, j: np.ndarray) -> int:
     return 3
 
 
-def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None):
+def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None, walls=(False, False)):
     """Periodic Kx x Ky quad mesh of the box domain=(x0, x1, y0, y1).
 
     ``mapping(X, Y)`` returns the displacement (dx, dy) of the lattice point
@@ -106,7 +106,9 @@ def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None):
     coordinates wrapped into the periodic box (identical bit patterns on both
     sides of every face, so fields evaluated there agree across faces).
     Element k = ky*Kx + kx; with rotate_seed the local frame of every element
-    is turned by a random number of quarter turns.
+    is turned by a random number of quarter turns. walls = (in x, in y):
+    the faces on x = x0, x1 (resp. y = y0, y1) become solid walls
+    (EToE = -1) instead of periodic, and those coordinates are not wrapped.
     """
     x0, x1, y0, y1 = domain
     Lx, Ly = x1 - x0, y1 - y0
@@ -121,8 +123,8 @@ def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None):
     ey = np.arange(Ky)[:, None] + (r[None, :] + 1.0) / 2.0
     Xc = x0 + Lx * ex / Kx
     Yc = y0 + Ly * ey / Ky
-    Xcw = np.where(Xc >= x1, Xc - Lx, Xc)
-    Ycw = np.where(Yc >= y1, Yc - Ly, Yc)
+    Xcw = Xc if walls[0] else np.where(Xc >= x1, Xc - Lx, Xc)
+    Ycw = Yc if walls[1] else np.where(Yc >= y1, Yc - Ly, Yc)
 
     jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")  # [j, i]
     ci_tab = np.stack([_local_to_canonical(N, q, ii, jj)[0] for q in range(4)])  # [4, n, n]
@@ -157,6 +159,14 @@ def periodic_mesh(N: int, Kx: int, Ky: int, domain, mapping, rotate_seed=None):
     EToE = nb.astype(np.int32)
     EToF = fn.astype(np.int32)
     flip = (rev_tab[rot[:, None], f] != rev_tab[rot[nb], fn]).astype(np.int32)
+    wall = np.zeros((K, 4), dtype=bool)
+    if walls[0]:
+        wall |= ((F == 1) & (kx[:, None] == Kx - 1)) | ((F == 3) & (kx[:, None] == 0))
+    if walls[1]:
+        wall |= ((F == 0) & (ky[:, None] == 0)) | ((F == 2) & (ky[:, None] == Ky - 1))
+    EToE[wall] = -1
+    EToF[wall] = 0
+    flip[wall] = 0
     return x, y, xw, yw, EToE, EToF, flip
 
 
@@ -313,6 +323,64 @@ def random_rough(N=3, K1=4, seed=0, rotate_seed=None, g=9.81, dry_fraction=0.0) 
     return p
 
 
+def lake_at_rest_walls(N=3, Kx=5, Ky=4, rotate_seed=None, g=9.81, walls=(True, True)) -> Problem:
+    """Lake at rest h + b = 1 in the curved box [0,2]^2 closed by solid walls
+    (x += 0.05 sin(pi x) sin(pi y), same for y, which keeps the walls
+    straight), over the kinked bathymetry of lake_at_rest_kinked."""
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, Kx, Ky, (0.0, 2.0, 0.0, 2.0), _sine_map(0.05, math.pi),
+                                           rotate_seed, walls)
+    r = np.sqrt((xw - 0.93) ** 2 + (yw - 1.07) ** 2)
+    b = 0.1 + 0.05 * np.sin(math.pi * xw) * np.cos(math.pi * yw) + 0.1 * np.maximum(0.0, 1.0 - r / 0.5)
+    z = np.zeros_like(b)
+    return Problem("lake_at_rest_walls", N, Kx, Ky, x, y, b, _state(1.0 - b, z, z), E, F, fl, g)
+
+
+def random_walls(N=3, Kx=4, Ky=3, seed=0, rotate_seed=None, g=9.81, walls=(True, True),
+                 rough=True) -> Problem:
+    """Random state (independent noise per node when rough, else smooth) on a
+    smooth random bathymetry in the curved box [0,2]^2 with solid walls."""
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, Kx, Ky, (0.0, 2.0, 0.0, 2.0), _sine_map(0.05, math.pi),
+                                           rotate_seed, walls)
+    rng = np.random.default_rng(seed)
+    b = 0.1 * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+    if rough:
+        h = 1.0 + 0.3 * rng.uniform(-1, 1, size=b.shape)
+        u = 0.5 * rng.uniform(-1, 1, size=b.shape)
+        v = 0.5 * rng.uniform(-1, 1, size=b.shape)
+    else:
+        h = 1.0 + 0.2 * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+        u = 0.5 * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+        v = 0.5 * _smooth_periodic_field(rng, xw, yw, 2.0, 2.0)
+    return Problem("random_walls", N, Kx, Ky, x, y, b, _state(h, u, v), E, F, fl, g)
+
+
+def dry_dam_break(N=3, K1=50, g=9.81, rotate_seed=None) -> Problem:
+    """Dam break into a dry region (Sec. 6.1.1): [-20,20]^2, solid walls at
+    x = +-20, periodic in y, flat bottom, h = 10 for x < 0 and 0 elsewhere,
+    at rest, Cartesian K1 x K1 mesh."""
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, K1, K1, (-20.0, 20.0, -20.0, 20.0),
+                                           lambda X, Y: (0.0 * X, 0.0 * Y), rotate_seed, (True, False))
+    b = np.zeros_like(xw)
+    h = np.where(xw < 0.0, 10.0, 0.0)
+    z = np.zeros_like(h)
+    return Problem("dry_dam_break", N, K1, K1, x, y, b, _state(h, z, z), E, F, fl, g)
+
+
+def three_mound_dam_break(N=3, Kx=150, Ky=100, g=9.81, rotate_seed=None) -> Problem:
+    """Dam break over three mounds (Sec. 6.3): [0,75] x [0,45] closed by solid
+    walls, h = 1.875 for x < 16 and dry elsewhere, at rest, bottom
+    b = max(0, M1, M2, M3) (Eq. ThreeMoundBottom), Cartesian Kx x Ky mesh."""
+    x, y, xw, yw, E, F, fl = periodic_mesh(N, Kx, Ky, (0.0, 75.0, 0.0, 45.0),
+                                           lambda X, Y: (0.0 * X, 0.0 * Y), rotate_seed, (True, True))
+    m1 = 1.0 - 0.1 * np.sqrt((xw - 30.0) ** 2 + (yw - 22.5) ** 2)
+    m2 = 1.0 - 0.1 * np.sqrt((xw - 30.0) ** 2 + (yw - 7.5) ** 2)
+    m3 = 2.8 - 0.28 * np.sqrt((xw - 47.5) ** 2 + (yw - 15.0) ** 2)
+    b = np.maximum(np.maximum(0.0, m1), np.maximum(m2, m3))
+    h = np.where(xw < 16.0, np.maximum(1.875 - b, 0.0), 0.0)
+    z = np.zeros_like(h)
+    return Problem("three_mound_dam_break", N, Kx, Ky, x, y, b, _state(h, z, z), E, F, fl, g)
+
+
 def ensemble_member(i: int, seed=5, sizes=(16, 96), degrees=(3, 5, 7), g=9.81) -> Problem:
     """Member i of the uneven ensemble: degree drawn from `degrees`, an s x s
     curved periodic [0,2]^2 mesh with s uniform in `sizes` (inclusive), a
@@ -346,4 +414,8 @@ CONFIGS = {
     "random_smooth": random_smooth,
     "random_rough": random_rough,
     "lake_at_rest_kinked": lake_at_rest_kinked,
+    "lake_at_rest_walls": lake_at_rest_walls,
+    "random_walls": random_walls,
+    "dry_dam_break": dry_dam_break,
+    "three_mound_dam_break": three_mound_dam_break,
 }
