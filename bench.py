@@ -44,9 +44,15 @@ def parse():
     ap.add_argument("--K1", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the split-form vs standard-form comparison")
     ap.add_argument("--ensemble", type=int, default=0,
                     help="members of the uneven ensemble (e.g. 256): one JSON line comparing the batched "
                          "ensemble with stepping every member through its own context")
+    ap.add_argument("--adjoint", action="store_true",
+                    help="gauge-misfit gradient by the adjoint (N=4, 64x64 quads, 200 steps, 64 gauges, "
+                         "checkpoints every 20 steps): one JSON line against the plain forward path")
     ap.add_argument("--sweep", default=None,
                     help="comma-separated degrees: one JSON line per degree at ~4.2M nodes "
                          "(step rate, right-hand-side rates, volume-kernel roofline)")
@@ -217,6 +223,57 @@ def run_reference(args):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def kernel_ms(ctx, W0, R, which="volume", reps=10):
+    """Mean event time of one launch of kernel class `which` over `reps`
+    right-hand sides (after two untimed ones)."""
+    import torch
+    for _ in range(2):
+        ctx.rhs(W0, R)
+    torch.cuda.synchronize()
+    ctx.timing(True)
+    for _ in range(reps):
+        ctx.rhs(W0, R)
+    torch.cuda.synchronize()
+    ms, cnt = ctx.timing_read(which)
+    ctx.timing(False)
+    return ms / max(cnt, 1)
+
+
+def rhs_rate(ctx, W0, R, nodes, reps=10):
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        ctx.rhs(W0, R)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        ctx.rhs(W0, R)
+    b.record(stream)
+    torch.cuda.synchronize()
+    return nodes / (a.elapsed_time(b) / reps * 1e-3)
+
+
+def split_vs_standard(prob, W0, R):
+    """The paper's GPU comparison (Eq. VolInt): the split-form volume kernel
+    against the standard one on the same state (ES interface flux, no AV, so
+    both kernels do only their volume work), and the full right-hand sides
+    with ES flux + AV in both forms."""
+    from paper_1804_02221_gb300 import swedg
+    out = {}
+    for name, vol in (("split", 0), ("standard", 1)):
+        c = swedg.SweContext.from_problem(prob, flux=1, volume=vol)
+        out[f"volume_ms_{name}"] = kernel_ms(c, W0, R)
+        c.close()
+        c = swedg.SweContext.from_problem(prob, flux=1, av=True, eps0=0.025, volume=vol)
+        out[f"rhs_es_av_node_updates_per_s_{name}"] = rhs_rate(c, W0, R, prob.nodes)
+        c.close()
+    out["volume_ratio_split_over_standard"] = out["volume_ms_split"] / out["volume_ms_standard"]
+    out["rhs_ratio_split_over_standard"] = (out["rhs_es_av_node_updates_per_s_standard"] /
+                                            out["rhs_es_av_node_updates_per_s_split"])
+    return out
+
+
 def sweep(args):
     """Degree sweep of the same workload recipe at ~4.2M nodes per degree."""
     import torch
@@ -266,10 +323,12 @@ def sweep(args):
         vol = vol_ms / vol_n
         achieved = volume_flops_per_node(N) * prob.nodes / (vol * 1e-3) / 1e12
         peak = fp64_peak_gflops(2070.0) / 1e3
+        cmp = split_vs_standard(prob, W0, R)
         print(json.dumps({"sweep": True, "N": N, "K": prob.K, "nodes": prob.nodes, "ms_per_step": ms,
                           "node_updates_per_s": RK_STAGES * prob.nodes / (ms * 1e-3),
                           "rhs_node_updates_per_s": rates, "volume_ms": vol,
-                          "volume_tflops": achieved, "volume_frac_at_2070MHz": achieved / peak}), flush=True)
+                          "volume_tflops": achieved, "volume_frac_at_2070MHz": achieved / peak,
+                          "split_vs_standard": cmp}), flush=True)
         ctx.close()
 
 
@@ -361,6 +420,79 @@ def ensemble_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def adjoint_bench(args):
+    """The adjoint workload: N = 4 on 64 x 64 curved periodic quads (lake at rest
+    with a hump, ES flux, AV in every element, LSRK4(5) at CFL 0.5), 200
+    adaptive steps, loss = squared h misfit at 64 seeded gauges against a run
+    over a perturbed bathymetry, gradients with respect to the initial state
+    and the bathymetry by the library's adjoint with checkpoints every 20
+    steps. Reported against the plain forward path on the same run."""
+    import numpy as np
+    import torch
+
+    from paper_1804_02221_gb300 import inputs as I
+    from paper_1804_02221_gb300 import swedg
+    torch.cuda.set_device(0)
+    stream = torch.cuda.current_stream()
+    N, K1, T, G, C = 4, 64, 200, 64, 20
+    p = I.lake_hump(N=N, K1=K1, amp=0.05)
+    kw = dict(flux=1, av=True, eps0=0.01, sigma_min=-301.0, sigma_max=-300.0, rk=0, cfl=0.5)
+    ctx = swedg.SweContext.from_problem(p, **kw)
+    rng = np.random.default_rng(3)
+    pts = rng.uniform(0.1, 1.9, size=(G, 2))
+    gw = I.gauge_weights(p, pts)
+    elem = torch.tensor([k for k, _ in gw], dtype=torch.int32, device="cuda")
+    wts = torch.tensor(np.stack([w.reshape(-1) for _, w in gw]), dtype=torch.float64, device="cuda")
+    q = I.Problem(p.name, p.N, p.Kx, p.Ky, p.x, p.y, p.b + 0.02 * np.sin(np.pi * p.x) * np.sin(np.pi * p.y),
+                  p.W, p.EToE, p.EToF, p.flip, p.g)
+    ctx_t = swedg.SweContext.from_problem(q, **kw)
+    target = torch.zeros(T, G, dtype=torch.float64, device="cuda")
+    swedg.GaugeLoss(ctx_t, elem, wts, torch.zeros_like(target), T).forward(torch.from_numpy(p.W).cuda(),
+                                                                           record=target)
+    W0 = torch.from_numpy(p.W).cuda()
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        out = fn()
+        b.record(stream)
+        torch.cuda.synchronize()
+        return a.elapsed_time(b), out
+
+    run = swedg.GaugeLoss(ctx, elem, wts, target, T, checkpoint=C)
+    run.forward(W0)
+    run.backward()
+    ms_fwd, loss = timed(lambda: run.forward(W0))
+    ms_bwd, (Wbar, bbar) = timed(lambda: run.backward())
+    # plain forward path: the same 200 steps without the gauges
+    W = W0.clone()
+    ms_plain, _ = timed(lambda: [ctx.step(W, dt, 1) for dt in run.dts])
+    # one right-hand side and its adjoint
+    R = torch.empty_like(W0)
+    Rbar = torch.randn_like(W0)
+    ms_rhs, _ = timed(lambda: [ctx.rhs(W0, R) for _ in range(20)])
+    Wb, bb = torch.zeros_like(W0), torch.zeros_like(W0[0])
+    ms_rhs_adj, _ = timed(lambda: [ctx.rhs_adjoint(W0, Rbar, Wb, bb) for _ in range(20)])
+    nodes = p.nodes
+    line = {
+        "adjoint": True, "metric": "RHS node-updates/s (FP64)", "unit": "node-updates/s",
+        "config": {"workload": f"gauge-misfit gradient, N={N} {K1}x{K1} curved periodic quads ({nodes} nodes), "
+                               f"{T} LSRK4(5) steps, {G} gauges, checkpoints every {C}, ES+AV"},
+        "loss": float(loss),
+        "forward": {"ms_per_step": ms_fwd / T, "value": RK_STAGES * nodes / (ms_fwd / T * 1e-3)},
+        "plain_forward": {"ms_per_step": ms_plain / T, "value": RK_STAGES * nodes / (ms_plain / T * 1e-3)},
+        "backward": {"ms_per_step": ms_bwd / T, "value": RK_STAGES * nodes / (ms_bwd / T * 1e-3),
+                     "note": "per step: checkpoint recomputation, stage recording, 5 stage adjoints"},
+        "gradient_over_plain": (ms_fwd + ms_bwd) / ms_plain,
+        "rhs": {"ms": ms_rhs / 20, "value": nodes / (ms_rhs / 20 * 1e-3)},
+        "rhs_adjoint": {"ms": ms_rhs_adj / 20, "value": nodes / (ms_rhs_adj / 20 * 1e-3),
+                        "note": "includes the forward recomputation of the right-hand side"},
+        "grad_norms": {"W0": float(Wbar.norm()), "b": float(bbar.norm())},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -371,6 +503,9 @@ def main():
         return
     if args.ensemble:
         ensemble_bench(args)
+        return
+    if args.adjoint:
+        adjoint_bench(args)
         return
     import numpy as np
     import torch
@@ -403,7 +538,8 @@ def main():
         ctx.step(Wd, 0.0, 1)
         ctx.integrals(Wd)  # mass, momenta and entropy, read back to the host
 
-    shapes = ctx.autotune(W0)  # launch shapes only: results are bitwise the same
+    # launch shapes only: results are bitwise the same for every shape
+    shapes = ctx.tuning() if args.no_autotune else ctx.autotune(W0)
 
     for _ in range(args.warmup):
         W.copy_(W0)
@@ -466,6 +602,9 @@ def main():
         torch.cuda.synchronize()
         rhs_rates[name] = nodes / (a.elapsed_time(b) / 10 * 1e-3)
 
+    # ---- the paper's comparison: split-form vs standard volume kernel ----
+    cmp = None if args.no_compare else split_vs_standard(prob, W0, R)
+
     # ---- reduce over ranks ----
     t_step, e2e_ms, value, e2e_value = combine_ranks(ms, e2e_ms, nodes, ws, dist, "cuda")
 
@@ -498,6 +637,7 @@ def main():
         "kernels": kernels,
         "rhs_only_node_updates_per_s": rhs_rates,
         "launch_shapes": {"volume_threads_per_block": shapes[0], "update_warps_per_block": shapes[1]},
+        "split_vs_standard": cmp,
         "scalar_updates_per_s": 3 * value,
     }
     if not args.no_cpu_baseline and ws == 1:

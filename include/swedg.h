@@ -13,8 +13,12 @@
  * Element faces: 0: eta=-1 (j=0), 1: xi=+1 (i=N), 2: eta=+1 (j=N),
  * 3: xi=-1 (i=0). Face node p runs along increasing xi (faces 0, 2) or eta
  * (faces 1, 3). Node p of face (k,f) meets node (flip ? N-p : p) of face
- * (EToE[k*4+f], EToF[k*4+f]). Every face must have a neighbour (periodic or
- * otherwise closed meshes); the connectivity must be reciprocal.
+ * (EToE[k*4+f], EToF[k*4+f]); the connectivity must be reciprocal.
+ * EToE[k*4+f] = -1 makes the face a solid wall (EToF, flip ignored there):
+ * the interface flux and the positivity time step take the mirror state
+ * (same h and b, normal velocity reversed), BR1 takes the own velocity as
+ * U* and no viscous flux crosses the wall. The paper uses solid walls in its
+ * dam-break cases but states no wall formula; this is the library's.
  *
  * Ownership: the caller owns W, R and every pointer it passes; a context owns
  * the geometry and the scratch buffers it allocates on the device at
@@ -61,7 +65,13 @@ typedef struct swe_ctx swe_ctx;
  * rk:        0 five-stage fourth-order 2N-storage Runge-Kutta (Carpenter &
  *            Kennedy), 1 SSPRK3 (Eq. RKSSP).
  * cfl:       CFL number of the time-step rule
- *            dt = cfl * 2/(N+1) * min_nodes J / (lambda_xi + lambda_eta). */
+ *            dt = cfl * 2/(N+1) * min_nodes J / (lambda_xi + lambda_eta).
+ * volume:    0 split-form volume term by flux differencing (Eq. fluxDiffFormF,
+ *            Eq. Fmij) with the well-balanced split source (Eq. SourceDisc);
+ *            1 the standard volume term of Eq. VolInt (second line), D applied
+ *            to the nodal contravariant fluxes, with the non-split source
+ *            -g h J grad b (the paper's comparison scheme: neither entropy
+ *            stable nor well balanced). */
 typedef struct {
     int flux;
     int av;
@@ -72,6 +82,7 @@ typedef struct {
     double h_tol;
     int rk;
     double cfl;
+    int volume;
 } swe_params;
 
 /* Build a context (Sec. 2.1: curvilinear map, metric terms, Jacobian
@@ -83,7 +94,8 @@ typedef struct {
  *   g > 0 gravity; p parameters (copied).
  * Uses the current CUDA device. 1 <= N <= SWE_NMAX, K >= 1.
  * Returns SWE_ERR_GEOM if J <= 0 at a node, SWE_ERR_ARG for bad
- * connectivity, sizes or parameters, SWE_ERR_CUDA on allocation failure. */
+ * connectivity (non-reciprocal, out of range other than the wall mark -1),
+ * sizes or parameters, SWE_ERR_CUDA on allocation failure. */
 int swe_create(int N, int K, const double* x, const double* y, const int32_t* EToE,
                const int32_t* EToF, const int32_t* flip, const double* b, double g,
                const swe_params* p, swe_ctx** out);
@@ -139,7 +151,7 @@ int swe_status(swe_ctx* ctx, int* bits, void* stream);
  * every kernel launch is bracketed by CUDA events on its stream;
  * swe_timing_read returns, for kernel class `which` (0 volume, 1 interface
  * flux, 2 primitives, 3 AV indicator/gradient, 4 viscous interface, 5 stage
- * update/limiter, 6 time step, 7 reductions), the summed event time in
+ * update/limiter, 6 time step, 7 reductions, 8 adjoint), the summed event time in
  * milliseconds and the launch count since swe_timing(ctx, 1) (synchronises).
  * swe_launches returns the number of kernels the context launched so far. */
 int swe_timing(swe_ctx* ctx, int on);
@@ -159,6 +171,41 @@ int64_t swe_launches(const swe_ctx* ctx);
 int swe_autotune(swe_ctx* ctx, const double* W, void* stream);
 int swe_get_tuning(const swe_ctx* ctx, int* vol_threads, int* upd_warps);
 int swe_set_tuning(swe_ctx* ctx, int vol_threads, int upd_warps);
+
+/* ---------------------------------------------------------------------------
+ * Adjoint (the paper has none; this is the library's). Vector-Jacobian
+ * products of the discrete operator for gradients with respect to the state
+ * and the bathymetry, exact up to rounding, with the decisions of the
+ * forward pass held fixed: the element viscosities eps_k (App. A), the
+ * limiter's active set (limited elements and the node of their minimum;
+ * theta of Eq. PosPres is differentiated), the nodes cut by h_tol and the
+ * step size. At dry nodes the velocity and the celerity have zero
+ * derivative. Split (entropy-stable) volume form only (volume = 0); other
+ * contexts get SWE_ERR_ARG. The first adjoint call allocates the adjoint's
+ * buffers (about 40 doubles per node plus 5 stage states).
+ *
+ * swe_rhs_adjoint: for R = swe_rhs(W), Wbar += (dR/dW)^T Rbar and, when bbar
+ * is not NULL, bbar += (dR/db)^T Rbar. W, Rbar, Wbar: device, 3*K*n*n;
+ * bbar: device, K*n*n. Asynchronous on `stream`.
+ *
+ * swe_step_adjoint: for one step W1 = step(W0, dt) of swe_step with the
+ * given dt > 0 (the size the forward step used), replaces Wbar (on entry the
+ * cotangent of W1) by the cotangent of W0, and adds the step's bathymetry
+ * cotangent to bbar (nullable). The step is recomputed from W0 (device,
+ * unchanged) with its decisions recorded, then swept in reverse stage by
+ * stage. Synchronises `stream`; SWE_ERR_NEG_MEAN if the recomputed step
+ * fails.
+ *
+ * swe_gauge_misfit: gauge values h_g = sum over the nodes of element elem[g]
+ * of wts[g][node] h (ngauge gauges; wts [ngauge][n*n] are interpolation
+ * weights; all device arrays). values (nullable) receives h_g; loss
+ * (nullable, one double) += sum_g (h_g - target_g)^2 (target nullable: 0);
+ * Wbar (nullable) += 2 (h_g - target_g) wts[g] on the h plane. Gauges are
+ * processed in order by one block (deterministic). Asynchronous. */
+int swe_rhs_adjoint(swe_ctx* ctx, const double* W, const double* Rbar, double* Wbar, double* bbar, void* stream);
+int swe_step_adjoint(swe_ctx* ctx, const double* W0, double dt, double* Wbar, double* bbar, void* stream);
+int swe_gauge_misfit(swe_ctx* ctx, const double* W, int ngauge, const int32_t* elem, const double* wts,
+                     const double* target, double* values, double* loss, double* Wbar, void* stream);
 
 /* Sizes of a context: N, K and the number of unique faces. */
 int swe_info(const swe_ctx* ctx, int* N, int* K, int* nfaces);
@@ -211,7 +258,7 @@ int swe_integrals_noalloc(int N, int K, const double* W, const double* wJ, const
 typedef struct swe_ens swe_ens;
 
 /* One instance (host arrays, copied at creation; layout as for swe_create).
- * EToE is local to the instance: 0 <= EToE < K. */
+ * EToE is local to the instance: 0 <= EToE < K, or -1 for a solid wall. */
 typedef struct {
     int N;
     int K;

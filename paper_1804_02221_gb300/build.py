@@ -17,8 +17,8 @@ ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libswedg.so")
-SOURCES = ["capi.cu", "basis.cpp", "k_volume.cu", "k_volume_64.cu", "k_volume_256.cu", "k_face.cu", "k_av.cu",
-           "noalloc.cu", "ensemble.cu"]
+SOURCES = ["capi.cu", "basis.cpp", "k_volume.cu", "k_volume_64.cu", "k_volume_256.cu", "k_volume_std.cu",
+           "k_face.cu", "k_av.cu", "k_adjoint.cu", "noalloc.cu", "ensemble.cu"]
 HEADERS = ["swe_internal.h", "kcommon.cuh", "k_volume.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

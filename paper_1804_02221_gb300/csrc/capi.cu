@@ -39,6 +39,8 @@ void init_device_tables(int device) {
     std::lock_guard<std::mutex> lock(mu);
     if (done.count(device)) return;
     swe::init_tables_volume();
+    swe::init_tables_volume_std();
+    swe::init_tables_adjoint();
     swe::init_tables_face();
     swe::init_tables_av();
     done.insert(device);
@@ -123,18 +125,19 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     if (!(g > 0.0) || !isfinite(g)) return fail(SWE_ERR_ARG, "swe_create: g must be positive");
     if (p->flux != 0 && p->flux != 1) return fail(SWE_ERR_ARG, "swe_create: flux must be 0 or 1");
     if (p->rk != 0 && p->rk != 1) return fail(SWE_ERR_ARG, "swe_create: rk must be 0 or 1");
+    if (p->volume != 0 && p->volume != 1) return fail(SWE_ERR_ARG, "swe_create: volume must be 0 or 1");
     if (p->av && !(p->eps0 >= 0.0)) return fail(SWE_ERR_ARG, "swe_create: eps0 must be >= 0");
     if (!isnan(p->h_tol) && !(p->h_tol >= 0.0)) return fail(SWE_ERR_ARG, "swe_create: h_tol must be >= 0");
     const int n = N + 1, nn = n * n;
     const long long KN = (long long)K * nn, KS = (long long)K * 4 * n;
     if (KN * 3 > 2147483647LL) return fail(SWE_ERR_ARG, "swe_create: mesh too large for 32-bit node ids");
-    // connectivity
+    // connectivity (EToE = -1: solid wall)
     for (int k = 0; k < K; ++k)
         for (int f = 0; f < 4; ++f) {
             const int kk = EToE[4 * k + f], ff = EToF[4 * k + f];
+            if (kk == -1) continue;
             if (kk < 0 || kk >= K || ff < 0 || ff > 3)
-                return fail(SWE_ERR_ARG, "swe_create: face without neighbour (boundary faces are not supported) at element " +
-                                             std::to_string(k));
+                return fail(SWE_ERR_ARG, "swe_create: EToE/EToF out of range at element " + std::to_string(k));
             if ((kk == k && ff == f) || EToE[4 * kk + ff] != k || EToF[4 * kk + ff] != f ||
                 flip[4 * kk + ff] != flip[4 * k + f] || (flip[4 * k + f] != 0 && flip[4 * k + f] != 1))
                 return fail(SWE_ERR_ARG, "swe_create: connectivity not reciprocal at element " + std::to_string(k));
@@ -198,6 +201,13 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
                     d3 += D[j * n + q] * tmp[3 * nn + q * n + i];
                 }
                 const long long id = o + j * n + i;
+                if (p->volume == 1) {
+                    // standard form: -g J grad b / J with J b_x = y_eta b_xi - y_xi b_eta,
+                    // J b_y = -x_eta b_xi + x_xi b_eta
+                    srcx[id] = -g * (axx[id] * bx + aex[id] * be) * rJ[id];
+                    srcy[id] = -g * (axy[id] * bx + aey[id] * be) * rJ[id];
+                    continue;
+                }
                 const double gx = axx[id] * bx + d0 + aex[id] * be + d1;
                 const double gy = axy[id] * bx + d2 + aey[id] * be + d3;
                 srcx[id] = -0.5 * g * gx * rJ[id];
@@ -213,9 +223,10 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     // kernel accumulates w_i w_j L with these, so that the partner node takes
     // the negative (w_q D_qi = -w_i D_iq, the SBP property).
     const int NP = N * (N + 1) / 2;
-    std::vector<double> pm((size_t)K * 2 * NP * 2 * n), fwJ(KN);
+    // (the standard volume form has no pairs)
+    std::vector<double> pm(p->volume == 1 ? 0 : (size_t)K * 2 * NP * 2 * n), fwJ(KN);
     for (long long a = 0; a < KN; ++a) fwJ[a] = -1.0 / wJ[a];
-    for (int k = 0; k < K; ++k)
+    for (int k = 0; k < K && p->volume == 0; ++k)
         for (int d = 0; d < 2; ++d) {
             const double* vx = d == 0 ? axx.data() : aex.data();
             const double* vy = d == 0 ? axy.data() : aey.data();
@@ -235,8 +246,8 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         }
 
     // ---- unique faces and element sides ----
-    std::vector<int32_t> f_im, f_ip, f_tm, f_tp, s_nb(KS);
-    std::vector<double> f_nx, f_ny, f_js, f_bm, f_bp, s_nx(KS), s_ny(KS), s_rwa(KS);
+    std::vector<int32_t> f_im, f_ip, f_tm, f_tp, s_nb(KS), w_im, w_tm;
+    std::vector<double> f_nx, f_ny, f_js, f_bm, f_bp, s_nx(KS), s_ny(KS), s_rwa(KS), w_nx, w_ny, w_js;
     const double w0 = w[0];
     auto outward = [&](int k, int f, int i, int j, double& nx, double& ny) {
         const long long id = (long long)k * nn + j * n + i;
@@ -247,10 +258,32 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
             default: nx = -axx[id]; ny = -axy[id]; break;
         }
     };
-    int nfaces = 0;
+    int nfaces = 0, nwall = 0;
     for (int k = 0; k < K; ++k)
         for (int f = 0; f < 4; ++f) {
             const int kk = EToE[4 * k + f], ff = EToF[4 * k + f], fl = flip[4 * k + f];
+            if (kk < 0) {
+                for (int pn = 0; pn < n; ++pn) {
+                    int i, j;
+                    face_node(N, f, pn, i, j);
+                    const long long own = (long long)k * nn + j * n + i;
+                    double nx, ny;
+                    outward(k, f, i, j, nx, ny);
+                    const double js = sqrt(nx * nx + ny * ny);
+                    const long long slot = ((long long)k * 4 + f) * n + pn;
+                    s_nb[slot] = -1;
+                    s_nx[slot] = nx / js;
+                    s_ny[slot] = ny / js;
+                    s_rwa[slot] = js / (w0 * Jv[own]);
+                    w_im.push_back((int32_t)own);
+                    w_tm.push_back((int32_t)slot);
+                    w_nx.push_back(nx / js);
+                    w_ny.push_back(ny / js);
+                    w_js.push_back(js);
+                }
+                ++nwall;
+                continue;
+            }
             for (int pn = 0; pn < n; ++pn) {
                 const int q = fl ? N - pn : pn;
                 int i, j, ii, jj;
@@ -300,6 +333,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     m.n = n;
     m.K = K;
     m.nfaces = nfaces;
+    m.nwall = nwall;
     m.KN = KN;
     m.KS = KS;
     m.g = g;
@@ -313,6 +347,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
     UP(m.f_ny, f_ny) UP(m.f_js, f_js) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
     UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
+    UP(m.w_im, w_im) UP(m.w_tm, w_tm) UP(m.w_nx, w_nx) UP(m.w_ny, w_ny) UP(m.w_js, w_js)
 #undef UP
     m.nae = nullptr;
     m.inst = nullptr;
@@ -351,6 +386,8 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     if (!shared_status) cudaMemset(W.status, 0, sizeof(int));
     swe::prepare_volume(c);
     cudaMemset(W.eps, 0, sizeof(double) * K);
+    // the viscous interface flux of solid-wall slots is zero and never rewritten
+    if (p->av) cudaMemset(W.Fvout, 0, sizeof(double) * 2 * KS);
     e2 = cudaDeviceSynchronize();
     if (e2 != cudaSuccess) {
         free_all(c);
@@ -582,6 +619,126 @@ extern "C" int swe_set_tuning(swe_ctx* c, int vol_threads, int upd_warps) {
     c->vol_tpb = vol_threads;
     c->upd_wpb = upd_warps;
     return SWE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Adjoint
+// ---------------------------------------------------------------------------
+
+namespace {
+
+int ensure_adjoint(swe_ctx* c) {
+    swe::AdjWork& A = c->adj;
+    if (A.ready) return SWE_OK;
+    const size_t KN = c->m.KN, KS = c->m.KS, K = c->m.K;
+    const int S = 5;  // stages of the longer scheme
+    cudaError_t e = cudaSuccess;
+#define ADJ_AL(dst, count)                                                  \
+    dst = dev_alloc(c, count, e);                                           \
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint: allocation");
+    ADJ_AL(A.Ga, 3 * KN) ADJ_AL(A.Guv, 2 * KN) ADJ_AL(A.Gsl, 4 * KS) ADJ_AL(A.Gfo, 3 * KS)
+    ADJ_AL(A.GUs, 2 * KS) ADJ_AL(A.Gfvt, 4 * KN) ADJ_AL(A.Gfvo, 2 * KS) ADJ_AL(A.Gfvtr, 4 * KS)
+    ADJ_AL(A.Gsrc, 2 * KN) ADJ_AL(A.Khb, 3 * KN) ADJ_AL(A.Rb, 3 * KN) ADJ_AL(A.Wnb, 3 * KN)
+    ADJ_AL(A.Ws, 3 * KN) ADJ_AL(A.Xs, S * 3 * KN) ADJ_AL(A.Ys, S * 3 * KN) ADJ_AL(A.Es, S * K)
+#undef ADJ_AL
+    void* q = nullptr;
+    e = cudaMalloc(&q, S * (K + KN) + 16);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint: allocation");
+    c->allocations.push_back(q);
+    A.act = static_cast<uint8_t*>(q);
+    A.cut = A.act + S * K;
+    q = nullptr;
+    e = cudaMalloc(&q, sizeof(int32_t) * S * K + 16);
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint: allocation");
+    c->allocations.push_back(q);
+    A.amin = static_cast<int32_t*>(q);
+    // wall slots of the side-node viscous cotangents are never written
+    e = cudaMemset(A.Gfvtr, 0, sizeof(double) * 4 * KS);
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint: initialisation");
+    A.stages = S;
+    A.ready = true;
+    return SWE_OK;
+}
+
+int adjoint_args(swe_ctx* c, const void* W, const void* cot, const void* Wbar, const char* where) {
+    if (!c || !W || !cot || !Wbar) return fail(SWE_ERR_ARG, std::string(where) + ": NULL argument");
+    if (c->p.volume != 0)
+        return fail(SWE_ERR_ARG, std::string(where) + ": the adjoint covers the split (entropy-stable) form only");
+    return ensure_adjoint(c);
+}
+
+}  // namespace
+
+extern "C" int swe_rhs_adjoint(swe_ctx* c, const double* W, const double* Rbar, double* Wbar, double* bbar,
+                               void* stream) {
+    if (int rc = adjoint_args(c, W, Rbar, Wbar, "swe_rhs_adjoint")) return rc;
+    cudaStream_t s = (cudaStream_t)stream;
+    // forward intermediates of W (viscosities, traces, fluxes), then the reverse sweep
+    swe::rhs_chain(c, W, c->w.R, s, nullptr, false);
+    swe::launch_rhs_adjoint(c, W, Rbar, Wbar, bbar, s);
+    return check_launch("swe_rhs_adjoint");
+}
+
+extern "C" int swe_step_adjoint(swe_ctx* c, const double* W0, double dt, double* Wbar, double* bbar,
+                                void* stream) {
+    if (int rc = adjoint_args(c, W0, W0, Wbar, "swe_step_adjoint")) return rc;
+    if (!(dt > 0.0)) return fail(SWE_ERR_ARG, "swe_step_adjoint: dt must be the step's positive size");
+    cudaStream_t s = (cudaStream_t)stream;
+    swe::AdjWork& A = c->adj;
+    const long long KN = c->m.KN, K = c->m.K, n3 = 3 * KN;
+    const int stages = c->p.rk == 0 ? 5 : 3;
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const int lim = c->p.limiter;
+    cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+    // ---- forward recomputation with the decisions recorded ----
+    cudaMemcpyAsync(A.Ws, W0, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (c->p.rk == 1) cudaMemcpyAsync(c->w.Wn, W0, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    swe::launch_prim(c, A.Ws, s, nullptr);
+    for (int st = 0; st < stages; ++st) {
+        cudaMemcpyAsync(A.Xs + st * n3, A.Ws, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        swe::rhs_chain(c, A.Ws, c->w.R, s, nullptr, true);
+        cudaMemcpyAsync(A.Es + st * K, c->w.eps, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        c->p.limiter = 0;  // the limiter runs separately, recording its plan
+        if (c->p.rk == 0)
+            swe::launch_update(c, 1, A.Ws, kLsrkA[st], kLsrkB[st], dt, nullptr, s, nullptr, true);
+        else
+            swe::launch_update(c, 2, A.Ws, ca[st], cb[st], dt, nullptr, s, nullptr, true);
+        c->p.limiter = lim;
+        cudaMemcpyAsync(A.Ys + st * n3, A.Ws, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (lim) swe::launch_limit_record(c, A.Ws, A.act + st * K, A.amin + st * K, A.cut + st * KN, s);
+    }
+    // ---- reverse sweep ----
+    cudaMemsetAsync(A.Khb, 0, n3 * sizeof(double), s);
+    if (c->p.rk == 1) cudaMemsetAsync(A.Wnb, 0, n3 * sizeof(double), s);
+    for (int st = stages - 1; st >= 0; --st) {
+        const double a = c->p.rk == 0 ? kLsrkA[st] : ca[st], b = c->p.rk == 0 ? kLsrkB[st] : cb[st];
+        swe::launch_update_adjoint(c, c->p.rk == 0 ? 1 : 2, Wbar, A.Ys + st * n3, A.act + st * K, A.amin + st * K,
+                                   A.cut + st * KN, A.Khb, A.Rb, A.Wnb, a, b, dt, s);
+        const double* X = A.Xs + st * n3;
+        swe::launch_prim(c, X, s, nullptr);
+        cudaMemcpyAsync(c->w.eps, A.Es + st * K, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        swe::rhs_chain(c, X, c->w.R, s, nullptr, true, true);
+        swe::launch_rhs_adjoint(c, X, A.Rb, Wbar, bbar, s);
+    }
+    if (c->p.rk == 1) swe::launch_axpy(c, n3, 1.0, A.Wnb, Wbar, s);
+    int rc = check_launch("swe_step_adjoint");
+    if (rc) return rc;
+    int status = 0;
+    cudaMemcpyAsync(&status, c->w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_step_adjoint");
+    if (status) return fail(SWE_ERR_NEG_MEAN, "swe_step_adjoint: the recomputed step failed (status bits set)");
+    return SWE_OK;
+}
+
+extern "C" int swe_gauge_misfit(swe_ctx* c, const double* W, int ngauge, const int32_t* elem, const double* wts,
+                                const double* target, double* values, double* loss, double* Wbar, void* stream) {
+    if (!c || !W || ngauge < 0 || (ngauge > 0 && (!elem || !wts)))
+        return fail(SWE_ERR_ARG, "swe_gauge_misfit: bad argument");
+    if (ngauge == 0) return SWE_OK;
+    swe::launch_gauge(c, W, ngauge, elem, wts, target, values, loss, Wbar, (cudaStream_t)stream);
+    return check_launch("swe_gauge_misfit");
 }
 
 // ---------------------------------------------------------------------------

@@ -90,9 +90,9 @@ extern "C" int swe_ens_create(int ninst, const swe_instance* in, double g, const
         if (q.N < 1 || q.N > SWE_NMAX || q.K < 1 || !q.x || !q.y || !q.b || !q.EToE || !q.EToF || !q.flip)
             return efail(SWE_ERR_ARG, "swe_ens_create: instance " + std::to_string(i) + ": bad size or NULL input");
         for (int64_t t = 0; t < 4 * (int64_t)q.K; ++t)
-            if (q.EToE[t] < 0 || q.EToE[t] >= q.K)
+            if (q.EToE[t] < -1 || q.EToE[t] >= q.K)
                 return efail(SWE_ERR_ARG, "swe_ens_create: instance " + std::to_string(i) +
-                                              ": EToE outside the instance (boundaries are not supported)");
+                                              ": EToE outside the instance (-1 marks a wall)");
         degrees.push_back(q.N);
     }
     std::sort(degrees.begin(), degrees.end());
@@ -139,7 +139,7 @@ extern "C" int swe_ens_create(int ninst, const swe_instance* in, double g, const
             memcpy(&y[e0 * nn], q.y, sizeof(double) * q.K * nn);
             memcpy(&b[e0 * nn], q.b, sizeof(double) * q.K * nn);
             for (int64_t t = 0; t < 4 * (int64_t)q.K; ++t) {
-                E2E[4 * e0 + t] = (int32_t)(q.EToE[t] + e0);
+                E2E[4 * e0 + t] = q.EToE[t] < 0 ? -1 : (int32_t)(q.EToE[t] + e0);
                 E2F[4 * e0 + t] = q.EToF[t];
                 fl[4 * e0 + t] = q.flip[t];
             }

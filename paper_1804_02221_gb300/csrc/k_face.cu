@@ -36,6 +36,30 @@ __global__ void k_prim(long long KN, const double* __restrict__ W, double* __res
 // g[[h+b]] - {c}[[u~]]). Writes +F to the owner's side slot and -F to the
 // neighbour's, and the BR1 interface values {u}, {v} to both.
 // ---------------------------------------------------------------------------
+// Flux in the normal frame from the rotated traces (u~, v~) of both sides.
+template <bool ES>
+__device__ __forceinline__ void normal_flux(double g, double hm, double hp, double utm, double utp, double vtm,
+                                            double vtp, double bm, double bp, double& F1, double& F2,
+                                            double& F3) {
+    const double ha = 0.5 * (hm + hp), ua = 0.5 * (utm + utp), va = 0.5 * (vtm + vtp);
+    const double h2a = 0.5 * fma(hm, hm, hp * hp);
+    F1 = ha * ua;
+    F2 = fma(F1, ua, 0.5 * g * h2a);
+    F3 = F1 * va;
+    if (ES) {
+        const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
+        const double gH = g * ((hp + bp) - (hm + bm));
+        const double dut = utp - utm, dvt = vtp - vtm;
+        const double r2g = 0.5 / g;
+        const double s1 = fabs(ua + ca) * r2g * fma(ca, dut, gH);
+        const double s3 = fabs(ua - ca) * r2g * fma(-ca, dut, gH);
+        const double d1 = s1 + s3;
+        F1 = fma(-0.5, d1, F1);
+        F2 = fma(-0.5, fma(ua, d1, ca * (s1 - s3)), F2);
+        F3 = fma(-0.5, fma(va, d1, fabs(ha * ua) * dvt), F3);
+    }
+}
+
 template <bool ES>
 __global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const double* __restrict__ uv,
                           double* __restrict__ Fout, double* __restrict__ Ustar, const int* stop) {
@@ -50,23 +74,8 @@ __global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const doub
         const double um = uv[im], vm = uv[m.KN + im], up = uv[ip], vp = uv[m.KN + ip];
         const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
         const double utp = fma(nx, up, ny * vp), vtp = fma(nx, vp, -ny * up);
-        const double ha = 0.5 * (hm + hp), ua = 0.5 * (utm + utp), va = 0.5 * (vtm + vtp);
-        const double h2a = 0.5 * fma(hm, hm, hp * hp);
-        double F1 = ha * ua;
-        double F2 = fma(F1, ua, 0.5 * g * h2a);
-        double F3 = F1 * va;
-        if (ES) {
-            const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
-            const double gH = g * ((hp + m.f_bp[t]) - (hm + m.f_bm[t]));
-            const double dut = utp - utm, dvt = vtp - vtm;
-            const double r2g = 0.5 / g;
-            const double s1 = fabs(ua + ca) * r2g * fma(ca, dut, gH);
-            const double s3 = fabs(ua - ca) * r2g * fma(-ca, dut, gH);
-            const double d1 = s1 + s3;
-            F1 = fma(-0.5, d1, F1);
-            F2 = fma(-0.5, fma(ua, d1, ca * (s1 - s3)), F2);
-            F3 = fma(-0.5, fma(va, d1, fabs(ha * ua) * dvt), F3);
-        }
+        double F1, F2, F3;
+        normal_flux<ES>(g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1, F2, F3);
         const double G1 = js * F1;
         const double G2 = js * fma(nx, F2, -ny * F3);
         const double G3 = js * fma(ny, F2, nx * F3);
@@ -81,6 +90,32 @@ __global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const doub
         Ustar[m.KS + tm] = vs;
         Ustar[tp] = us;
         Ustar[m.KS + tp] = vs;
+    }
+}
+
+// Solid walls: the flux against the mirror state (same h and b, normal
+// velocity reversed) to the own side slot only; BR1 takes the own velocity
+// as U* (no gradient lift). The viscous interface flux of a wall slot is
+// zero and is never written after creation.
+template <bool ES>
+__global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double* __restrict__ uv,
+                       double* __restrict__ Fout, double* __restrict__ Ustar, const int* stop) {
+    if (stopped(stop)) return;
+    const long long total = (long long)m.nwall * m.n;
+    const double g = m.g;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long im = m.w_im[t], tm = m.w_tm[t];
+        const double nx = m.w_nx[t], ny = m.w_ny[t], js = m.w_js[t];
+        const double hm = W[im], um = uv[im], vm = uv[m.KN + im], bm = m.bn[im];
+        const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
+        double F1, F2, F3;
+        normal_flux<ES>(g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1, F2, F3);
+        Fout[tm] = js * F1;
+        Fout[m.KS + tm] = js * fma(nx, F2, -ny * F3);
+        Fout[2 * m.KS + tm] = js * fma(ny, F2, nx * F3);
+        Ustar[tm] = um;
+        Ustar[m.KS + tm] = vm;
     }
 }
 
@@ -323,11 +358,13 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
         const int j = (f == 1 || f == 3) ? p : (f == 2 ? N : 0);
         const long long own = k * nn + j * n + i;
         const long long slot = k * 4 * n + sn;
-        const long long nb = m.s_nb[slot];
+        const long long sb = m.s_nb[slot];
+        const bool wall = sb < 0;  // solid wall: the mirror state
+        const long long nb = wall ? own : sb;
         const double nx = m.s_nx[slot], ny = m.s_ny[slot], rwa = m.s_rwa[slot];
         const double hm = a.W[own], hp = a.W[nb];
         const double utm = fma(nx, a.uv[own], ny * a.uv[m.KN + own]);
-        const double utp = fma(nx, a.uv[nb], ny * a.uv[m.KN + nb]);
+        const double utp = wall ? -utm : fma(nx, a.uv[nb], ny * a.uv[m.KN + nb]);
         const double ua = 0.5 * (utm + utp);
         const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
         const double ap = fabs(ua + ca), am = fabs(ua - ca);
@@ -491,15 +528,26 @@ void launch_prim(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
 
 void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
     const long long total = (long long)c->m.nfaces * c->m.n;
-    Timed tm(c, KC_FACE, s);
-    if (c->p.flux)
-        k_surface<true><<<grid_for(total, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
-    else
-        k_surface<false><<<grid_for(total, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
+    if (total > 0) {
+        Timed tm(c, KC_FACE, s);
+        if (c->p.flux)
+            k_surface<true><<<grid_for(total, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
+        else
+            k_surface<false><<<grid_for(total, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
+    }
+    const long long walls = (long long)c->m.nwall * c->m.n;
+    if (walls > 0) {
+        Timed tm(c, KC_FACE, s);
+        if (c->p.flux)
+            k_wall<true><<<grid_for(walls, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
+        else
+            k_wall<false><<<grid_for(walls, 128), 128, 0, s>>>(c->m, W, c->w.uv, c->w.Fout, c->w.Ustar, stop);
+    }
 }
 
 void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop) {
     const long long total = (long long)c->m.nfaces * c->m.n;
+    if (total == 0) return;
     Timed tm(c, KC_VFACE, s);
     k_visc_face<<<grid_for(total, 128), 128, 0, s>>>(c->m, c->w.Fvtr, c->w.Fvout, stop);
 }

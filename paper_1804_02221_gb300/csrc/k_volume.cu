@@ -26,6 +26,10 @@ bool volume_shape_valid(int N, int tpb) {
 }
 
 void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop) {
+    if (c->p.volume == 1) {
+        launch_volume_std(c, W, R, s, stop);
+        return;
+    }
     bool done = false;
     if (c->vol_tpb == 64) done = volume_launch_64(c, W, R, s, stop);
     else if (c->vol_tpb == 256) done = volume_launch_256(c, W, R, s, stop);

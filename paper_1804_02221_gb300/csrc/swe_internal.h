@@ -60,7 +60,8 @@ enum KernelClass {
     KC_UPDATE = 5,
     KC_DT = 6,
     KC_REDUCE = 7,
-    KC_COUNT = 8
+    KC_ADJ = 8,
+    KC_COUNT = 9
 };
 
 // Device-side data of one context. Nodal arrays are [K][n][n] planes,
@@ -98,10 +99,18 @@ struct DeviceMesh {
     const double* f_bm;    // bathymetry on both sides
     const double* f_bp;
     // per element side node
-    const int32_t* s_nb;   // node id of the neighbour's matching node
+    const int32_t* s_nb;   // node id of the neighbour's matching node (-1: solid wall)
     const double* s_nx;    // own outward unit normal
     const double* s_ny;
     const double* s_rwa;   // 1/(omega_0 a), a = J/Jsurf (Lemma PosPres)
+    // per solid-wall face node (nwall wall faces): own node id, own side
+    // slot, outward unit normal, surface Jacobian
+    int nwall;
+    const int32_t* w_im;
+    const int32_t* w_tm;
+    const double* w_nx;
+    const double* w_ny;
+    const double* w_js;
     // ensembles: instance of every element (nullable: one instance), count
     const int32_t* inst;
     int ninst;
@@ -124,6 +133,31 @@ struct Work {
     int* status;    // [1] status bits (shared by the groups of an ensemble)
 };
 
+// Buffers of the adjoint (allocated at the first adjoint call).
+struct AdjWork {
+    bool ready = false;
+    int stages = 0;
+    double* Ga = nullptr;     // [3][KN] node cotangents of (h, hu, hv), direct paths
+    double* Guv = nullptr;    // [2][KN] node cotangents of (u, v)
+    double* Gsl = nullptr;    // [4][KS] side-slot cotangents of (h, u, v, b)
+    double* Gfo = nullptr;    // [3][KS] interface-flux cotangents
+    double* GUs = nullptr;    // [2][KS] BR1 interface-value cotangents
+    double* Gfvt = nullptr;   // [4][KN] contravariant viscous-flux cotangents
+    double* Gfvo = nullptr;   // [2][KS] viscous interface-flux cotangents
+    double* Gfvtr = nullptr;  // [4][KS] side-node viscous-flux cotangents (wall slots stay 0)
+    double* Gsrc = nullptr;   // [2][KN] source-coefficient cotangents
+    double* Khb = nullptr;    // [3][KN] 2N-storage register cotangent
+    double* Rb = nullptr;     // [3][KN] right-hand-side cotangent of a stage
+    double* Wnb = nullptr;    // [3][KN] step-start cotangent (SSP)
+    double* Ws = nullptr;     // [3][KN] recomputed state
+    double* Xs = nullptr;     // [stages][3][KN] stage inputs
+    double* Ys = nullptr;     // [stages][3][KN] pre-limit stage results
+    double* Es = nullptr;     // [stages][K] element viscosities
+    uint8_t* act = nullptr;   // [stages][K] limited elements
+    int32_t* amin = nullptr;  // [stages][K] node of the minimum
+    uint8_t* cut = nullptr;   // [stages][KN] h_tol cut
+};
+
 }  // namespace swe
 
 struct swe_ctx {
@@ -133,6 +167,7 @@ struct swe_ctx {
     double sigma_min = 0, sigma_max = 0, h_tol = 1e-4;
     swe::DeviceMesh m{};
     swe::Work w{};
+    swe::AdjWork adj{};
     std::vector<void*> allocations;
     int64_t launches = 0;
     // launch shapes (swe_autotune): volume threads per block, update warps per block
@@ -151,6 +186,8 @@ namespace swe {
 void init_tables_volume();
 void init_tables_face();
 void init_tables_av();
+void init_tables_volume_std();
+void init_tables_adjoint();
 
 // Per-process kernel attributes of the context's degree (called at creation,
 // so that later launches, also inside a stream capture, change no state).
@@ -171,7 +208,10 @@ bool volume_shape_valid(int N, int tpb);
 
 void launch_prim(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+// Volume term of the context's form (p.volume): the split-form kernel in the
+// tuned launch shape, or the standard-form kernel.
 void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
+void launch_volume_std(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
 EpsParams eps_params(const swe_ctx* c);
 // eps_given: the element viscosities of W are already in the work buffer
 void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given);
@@ -205,6 +245,18 @@ void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop
 // Pick the fastest launch shapes of the volume kernel and the stage update
 // for this context on W (scratch buffers only); synchronises s.
 int autotune_ctx(swe_ctx* c, const double* W, cudaStream_t s);
+
+// Adjoint launchers (k_adjoint.cu). launch_rhs_adjoint expects the forward
+// intermediates of W in the work buffers (rhs_chain just ran on W) and adds
+// (dR/dW)^T Rb to Wbar and (dR/db)^T Rb to bbar (nullable).
+void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* Wbar, double* bbar, cudaStream_t s);
+void launch_limit_record(swe_ctx* c, double* W, uint8_t* act, int32_t* amin, uint8_t* cut, cudaStream_t s);
+void launch_update_adjoint(swe_ctx* c, int mode, double* Wb, const double* Y, const uint8_t* act,
+                           const int32_t* amin, const uint8_t* cut, double* Khb, double* Rb, double* Wnb, double a,
+                           double b, double dt, cudaStream_t s);
+void launch_gauge(swe_ctx* c, const double* W, int ng, const int32_t* elem, const double* wts,
+                  const double* target, double* values, double* loss, double* Wb, cudaStream_t s);
+void launch_axpy(swe_ctx* c, long long count, double a, const double* x, double* y, cudaStream_t s);
 
 // Context construction (swe_create; ensembles pass an instance map and a
 // status word shared by their groups).

@@ -407,6 +407,62 @@ def ensemble(ninst=256, seed=5, sizes=(16, 96), degrees=(3, 5, 7), g=9.81) -> li
     return [ensemble_member(i, seed, sizes, degrees, g) for i in range(ninst)]
 
 
+def gauge_weights(prob, points):
+    """Gauges of a loss functional: for each physical point the element that
+    contains it and the (n, n) tensor-product Lagrange weights at its
+    reference coordinates (found by Newton on the element map), so that a
+    nodal field's value there is sum(weights * field[element])."""
+    N, n = prob.N, prob.N + 1
+    xi = lgl_points(N)
+
+    def lag(r):
+        L = np.ones(n)
+        for j in range(n):
+            for m in range(n):
+                if m != j:
+                    L[j] *= (r - xi[m]) / (xi[j] - xi[m])
+        return L
+
+    def dlag(r):
+        d = np.zeros(n)
+        for j in range(n):
+            for l in range(n):
+                if l == j:
+                    continue
+                t = 1.0 / (xi[j] - xi[l])
+                for m in range(n):
+                    if m != j and m != l:
+                        t *= (r - xi[m]) / (xi[j] - xi[m])
+                d[j] += t
+        return d
+
+    cx = prob.x.mean(axis=(1, 2))
+    cy = prob.y.mean(axis=(1, 2))
+    out = []
+    for (px, py) in points:
+        order = np.argsort((cx - px) ** 2 + (cy - py) ** 2)
+        for k in order[:9]:
+            r = s = 0.0
+            for _ in range(50):
+                Lr, Ls, dLr, dLs = lag(r), lag(s), dlag(r), dlag(s)
+                X = Ls @ prob.x[k] @ Lr
+                Y = Ls @ prob.y[k] @ Lr
+                Xr, Xs = Ls @ prob.x[k] @ dLr, dLs @ prob.x[k] @ Lr
+                Yr, Ys = Ls @ prob.y[k] @ dLr, dLs @ prob.y[k] @ Lr
+                det = Xr * Ys - Xs * Yr
+                dr = (Ys * (px - X) - Xs * (py - Y)) / det
+                ds = (-Yr * (px - X) + Xr * (py - Y)) / det
+                r, s = r + dr, s + ds
+                if abs(dr) + abs(ds) < 1e-15:
+                    break
+            if abs(r) <= 1 + 1e-12 and abs(s) <= 1 + 1e-12:
+                out.append((int(k), np.outer(lag(s), lag(r))))
+                break
+        else:
+            raise ValueError(f"gauge point {(px, py)} not found in the mesh")
+    return out
+
+
 CONFIGS = {
     "lake_hump": lake_hump,
     "dam_break": dam_break,

@@ -17,21 +17,22 @@ from . import build as _build
 
 OK, ERR_ARG, ERR_GEOM, ERR_NEG_MEAN, ERR_NONFINITE, ERR_CUDA = 0, -1, -2, -3, -4, -5
 KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "update": 5, "dt": 6,
-                  "reduce": 7}
+                  "reduce": 7, "adjoint": 8}
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_read",
            "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals",
            "swe_ens_create", "swe_ens_destroy", "swe_ens_size", "swe_ens_layout", "swe_ens_rhs",
            "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches", "swe_autotune",
-           "swe_get_tuning", "swe_set_tuning", "swe_ens_autotune", "swe_ens_group"]
+           "swe_get_tuning", "swe_set_tuning", "swe_ens_autotune", "swe_ens_group", "swe_rhs_adjoint",
+           "swe_step_adjoint", "swe_gauge_misfit"]
 
 
 class Params(ctypes.Structure):
     _fields_ = [("flux", ctypes.c_int), ("av", ctypes.c_int), ("eps0", ctypes.c_double),
                 ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
                 ("limiter", ctypes.c_int), ("h_tol", ctypes.c_double), ("rk", ctypes.c_int),
-                ("cfl", ctypes.c_double)]
+                ("cfl", ctypes.c_double), ("volume", ctypes.c_int)]
 
 
 class Instance(ctypes.Structure):
@@ -101,6 +102,9 @@ def lib():
     L.swe_set_tuning.argtypes = [vp, ctypes.c_int, ctypes.c_int]
     L.swe_ens_autotune.argtypes = [vp, vp, vp]
     L.swe_ens_group.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip]
+    L.swe_rhs_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
+    L.swe_step_adjoint.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
+    L.swe_gauge_misfit.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = ctypes.c_char_p
     _lib = L
@@ -140,14 +144,14 @@ class SweContext:
     """One mesh + parameter set on the current CUDA device (swe_create)."""
 
     def __init__(self, N, K, x, y, EToE, EToF, flip, b, g=9.81, flux=1, av=False, eps0=0.0,
-                 sigma_min=math.nan, sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5):
+                 sigma_min=math.nan, sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("swedg needs a CUDA device; there is no CPU path")
         L = lib()
         self.N, self.K, self.n = int(N), int(K), int(N) + 1
         self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
-                             int(limiter), float(h_tol), int(rk), float(cfl))
+                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume))
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, b)]
         cons = [np.ascontiguousarray(a, dtype=np.int32) for a in (EToE, EToF, flip)]
         d = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -239,6 +243,42 @@ class SweContext:
     def launches(self):
         return int(lib().swe_launches(self._h))
 
+    # ---- adjoint ----------------------------------------------------------
+    def _plane(self, b):
+        import torch
+        if b is None:
+            return ctypes.c_void_p()
+        if not (isinstance(b, torch.Tensor) and b.is_cuda and b.dtype == torch.float64 and b.is_contiguous()
+                and tuple(b.shape) == (self.K, self.n, self.n)):
+            raise ValueError("bathymetry cotangent must be a contiguous float64 CUDA tensor [K, n, n]")
+        return ctypes.c_void_p(b.data_ptr())
+
+    def rhs_adjoint(self, W, Rbar, Wbar=None, bbar=None, stream=None):
+        """Wbar += (dR/dW)^T Rbar, bbar += (dR/db)^T Rbar (allocated as zeros
+        when not given); returns (Wbar, bbar)."""
+        import torch
+        if Wbar is None:
+            Wbar = torch.zeros_like(W)
+        if bbar is None:
+            bbar = torch.zeros((self.K, self.n, self.n), dtype=torch.float64, device=W.device)
+        _check(lib().swe_rhs_adjoint(self._h, self._state(W), self._state(Rbar), self._state(Wbar),
+                                     self._plane(bbar), _stream(stream)))
+        return Wbar, bbar
+
+    def step_adjoint(self, W0, dt, Wbar, bbar=None, stream=None):
+        """Wbar (cotangent of step(W0, dt)) becomes the cotangent of W0; the
+        step's bathymetry cotangent is added to bbar (if given)."""
+        _check(lib().swe_step_adjoint(self._h, self._state(W0), float(dt), self._state(Wbar), self._plane(bbar),
+                                      _stream(stream)))
+        return Wbar
+
+    def gauge_misfit(self, W, elem, wts, target=None, values=None, loss=None, Wbar=None, stream=None):
+        """swe_gauge_misfit on device tensors (elem int32 [G], wts [G, n*n])."""
+        ptr = lambda t: ctypes.c_void_p(t.data_ptr()) if t is not None else ctypes.c_void_p()
+        _check(lib().swe_gauge_misfit(self._h, self._state(W), int(elem.numel()), ptr(elem), ptr(wts), ptr(target),
+                                      ptr(values), ptr(loss), ptr(Wbar) if Wbar is None else self._state(Wbar),
+                                      _stream(stream)))
+
     def autotune(self, W, stream=None):
         """Time the launch shapes on W and keep the fastest; returns them."""
         _check(lib().swe_autotune(self._h, self._state(W), _stream(stream)))
@@ -264,13 +304,13 @@ class SweEnsemble:
     `view(W, i)` is instance i's (3, K, n, n) view into it."""
 
     def __init__(self, problems, g=9.81, flux=1, av=False, eps0=0.0, sigma_min=math.nan,
-                 sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5):
+                 sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("swedg needs a CUDA device; there is no CPU path")
         L = lib()
         self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
-                             int(limiter), float(h_tol), int(rk), float(cfl))
+                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume))
         self.ninst = len(problems)
         keep = []
         arr = (Instance * self.ninst)()
@@ -367,3 +407,78 @@ class SweEnsemble:
             _check(lib().swe_ens_group(self._h, g, *[ctypes.byref(x) for x in v]))
             out.append(tuple(x.value for x in v))
         return out
+
+
+class GaugeLoss:
+    """Loss L = sum over steps t = 1..T and gauges g of (h_g(W_t) - target_{t,g})^2
+    of an adaptive run of `nsteps` swe_step steps from W0, and its gradient
+    with respect to W0 and the bathymetry through the library's adjoint
+    (swe_step_adjoint, swe_gauge_misfit), recomputing states from checkpoints
+    taken every `checkpoint` steps. The step sizes of the forward run are
+    kept and reused by the reverse sweep. Device tensors: elem int32 [G],
+    wts float64 [G, n*n], targets float64 [T, G]."""
+
+    def __init__(self, ctx, elem, wts, targets, nsteps, checkpoint=20):
+        self.ctx, self.elem, self.wts = ctx, elem, wts
+        self.targets, self.nsteps, self.checkpoint = targets, int(nsteps), max(1, int(checkpoint))
+
+    def forward(self, W0, record=None):
+        """Runs the steps; returns the loss (device scalar tensor). record
+        (optional [T, G] tensor) receives the gauge values."""
+        import torch
+        ctx = self.ctx
+        W = W0.clone()
+        loss = torch.zeros(1, dtype=torch.float64, device=W0.device)
+        self.dts, self.ckpt = [], {0: W0.clone()}
+        for t in range(self.nsteps):
+            _, dt = ctx.step(W, 0.0, 1)
+            self.dts.append(dt)
+            vals = None if record is None else record[t]
+            ctx.gauge_misfit(W, self.elem, self.wts, target=self.targets[t], values=vals, loss=loss)
+            if (t + 1) % self.checkpoint == 0 and t + 1 < self.nsteps:
+                self.ckpt[t + 1] = W.clone()
+        return loss[0]
+
+    def backward(self, grad_b=True):
+        """(dL/dW0, dL/db) of the last forward run."""
+        import torch
+        ctx = self.ctx
+        W0 = self.ckpt[0]
+        Wbar = torch.zeros_like(W0)
+        bbar = torch.zeros((ctx.K, ctx.n, ctx.n), dtype=torch.float64, device=W0.device) if grad_b else None
+        T = self.nsteps
+        starts = sorted(self.ckpt)
+        for c0 in reversed(starts):
+            nxt = [s for s in starts if s > c0]
+            c1 = nxt[0] if nxt else T
+            # states W_{c0} .. W_{c1} of the segment, with the recorded step sizes
+            states = [self.ckpt[c0].clone()]
+            for t in range(c0, c1):
+                W = states[-1].clone()
+                ctx.step(W, self.dts[t], 1)
+                states.append(W)
+            for t in range(c1, c0, -1):
+                ctx.gauge_misfit(states[t - c0], self.elem, self.wts, target=self.targets[t - 1], Wbar=Wbar)
+                ctx.step_adjoint(states[t - 1 - c0], self.dts[t - 1], Wbar, bbar)
+        return Wbar, bbar
+
+
+def gauge_loss(ctx, W0, b, elem, wts, targets, nsteps, checkpoint=20):
+    """torch.autograd entry point: loss of GaugeLoss with gradients flowing to
+    W0 and to b (the bathymetry tensor the context was created with)."""
+    import torch
+
+    class _Fn(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, W0_, b_):
+            run = GaugeLoss(ctx, elem, wts, targets, nsteps, checkpoint)
+            loss = run.forward(W0_)
+            fctx.run = run
+            return loss
+
+        @staticmethod
+        def backward(fctx, g):
+            Wbar, bbar = fctx.run.backward(grad_b=True)
+            return g * Wbar, (g * bbar).to(b.device).reshape(b.shape)
+
+    return _Fn.apply(W0, b)

@@ -11,7 +11,8 @@ from paper_1804_02221_gb300 import inputs as I
 
 torch = pytest.importorskip("torch")
 from oracle.adjoint_ref import LSRK_A as O_LSRK_A, LSRK_B as O_LSRK_B  # noqa: E402
-from oracle.adjoint_ref import Twin, gauge_weights  # noqa: E402
+from oracle.adjoint_ref import Twin  # noqa: E402
+gauge_weights = I.gauge_weights
 
 AV_FLAT = dict(eps0=0.02, sigma_min=-301.0, sigma_max=-300.0)  # eps = eps0 in every element
 
