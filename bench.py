@@ -475,6 +475,17 @@ def adjoint_bench(args):
     Wb, bb = torch.zeros_like(W0), torch.zeros_like(W0[0])
     ms_rhs_adj, _ = timed(lambda: [ctx.rhs_adjoint(W0, Rbar, Wb, bb) for _ in range(20)])
     nodes = p.nodes
+    # one right-hand side and its adjoint at the main workload's size (N=7, 4.19M nodes)
+    big = I.dam_break(N=7)
+    cb = swedg.SweContext.from_problem(big, flux=1, av=True, eps0=0.025)
+    Wd = torch.from_numpy(big.W).cuda()
+    Rd, Rbd = torch.empty_like(Wd), torch.randn_like(Wd)
+    Wbd, bbd = torch.zeros_like(Wd), torch.zeros_like(Wd[0])
+    cb.rhs(Wd, Rd)
+    cb.rhs_adjoint(Wd, Rbd, Wbd, bbd)
+    ms_big, _ = timed(lambda: [cb.rhs(Wd, Rd) for _ in range(5)])
+    ms_big_adj, _ = timed(lambda: [cb.rhs_adjoint(Wd, Rbd, Wbd, bbd) for _ in range(5)])
+    cb.close()
     line = {
         "adjoint": True, "metric": "RHS node-updates/s (FP64)", "unit": "node-updates/s",
         "config": {"workload": f"gauge-misfit gradient, N={N} {K1}x{K1} curved periodic quads ({nodes} nodes), "
@@ -489,6 +500,11 @@ def adjoint_bench(args):
         "rhs_adjoint": {"ms": ms_rhs_adj / 20, "value": nodes / (ms_rhs_adj / 20 * 1e-3),
                         "note": "includes the forward recomputation of the right-hand side"},
         "grad_norms": {"W0": float(Wbar.norm()), "b": float(bbar.norm())},
+        "large": {"workload": f"dam_break N=7 256x256 ({big.nodes} nodes), ES+AV",
+                  "rhs_ms": ms_big / 5, "rhs_adjoint_ms": ms_big_adj / 5,
+                  "rhs_value": big.nodes / (ms_big / 5 * 1e-3),
+                  "rhs_adjoint_value": big.nodes / (ms_big_adj / 5 * 1e-3),
+                  "ratio": ms_big_adj / ms_big},
     }
     print(json.dumps(line), flush=True)
 

@@ -670,12 +670,20 @@ int adjoint_args(swe_ctx* c, const void* W, const void* cot, const void* Wbar, c
 
 }  // namespace
 
+// The forward quantities the reverse sweep reads at W: velocities, BR1
+// interface values and, unless given, the element viscosities. The volume
+// term and the viscous fluxes themselves are not needed.
+static void adjoint_prerequisites(swe_ctx* c, const double* W, cudaStream_t s, bool eps_given) {
+    swe::launch_prim(c, W, s, nullptr);
+    swe::launch_surface(c, W, s, nullptr);
+    if (c->p.av && !eps_given) swe::launch_av(c, W, s, nullptr, false);
+}
+
 extern "C" int swe_rhs_adjoint(swe_ctx* c, const double* W, const double* Rbar, double* Wbar, double* bbar,
                                void* stream) {
     if (int rc = adjoint_args(c, W, Rbar, Wbar, "swe_rhs_adjoint")) return rc;
     cudaStream_t s = (cudaStream_t)stream;
-    // forward intermediates of W (viscosities, traces, fluxes), then the reverse sweep
-    swe::rhs_chain(c, W, c->w.R, s, nullptr, false);
+    adjoint_prerequisites(c, W, s, false);
     swe::launch_rhs_adjoint(c, W, Rbar, Wbar, bbar, s);
     return check_launch("swe_rhs_adjoint");
 }
@@ -716,9 +724,8 @@ extern "C" int swe_step_adjoint(swe_ctx* c, const double* W0, double dt, double*
         swe::launch_update_adjoint(c, c->p.rk == 0 ? 1 : 2, Wbar, A.Ys + st * n3, A.act + st * K, A.amin + st * K,
                                    A.cut + st * KN, A.Khb, A.Rb, A.Wnb, a, b, dt, s);
         const double* X = A.Xs + st * n3;
-        swe::launch_prim(c, X, s, nullptr);
         cudaMemcpyAsync(c->w.eps, A.Es + st * K, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        swe::rhs_chain(c, X, c->w.R, s, nullptr, true, true);
+        adjoint_prerequisites(c, X, s, true);
         swe::launch_rhs_adjoint(c, X, A.Rb, Wbar, bbar, s);
     }
     if (c->p.rk == 1) swe::launch_axpy(c, n3, 1.0, A.Wnb, Wbar, s);
