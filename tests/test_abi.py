@@ -36,3 +36,66 @@ def test_library_builds_and_exports_every_declared_symbol():
 def test_last_error_callable_without_gpu():
     lib = swedg.lib()
     assert isinstance(lib.swe_last_error(), bytes)
+
+
+# ---------------------------------------------------------------------------
+# Argument checks that return before any CUDA call (host logic, no GPU)
+# ---------------------------------------------------------------------------
+
+def _dp():
+    return ctypes.POINTER(ctypes.c_double)
+
+
+def _call_create(N, K, params=None, n_elem=1):
+    lib = swedg.lib()
+    nn = (N + 1) ** 2
+    x = (ctypes.c_double * (nn * n_elem))()
+    i4 = (ctypes.c_int32 * (4 * n_elem))()
+    p = params or swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 0)
+    h = ctypes.c_void_p()
+    rc = lib.swe_create(N, K, x, x, i4, i4, i4, x, 9.81, ctypes.byref(p), ctypes.byref(h))
+    return rc, lib.swe_last_error().decode()
+
+
+def test_create_rejects_empty_mesh_and_bad_degrees():
+    for N, K in ((3, 0), (3, -1), (0, 4), (13, 4)):
+        rc, msg = _call_create(N, K)
+        assert rc == swedg.ERR_ARG, (N, K, msg)
+
+
+def test_create_rejects_meshes_beyond_32_bit_node_ids():
+    # N = 12 (169 nodes per element): 3 K n^2 > 2^31 - 1 from K = 4,235,629 on;
+    # the size check runs before any input array is read
+    rc, msg = _call_create(12, 4_300_000)
+    assert rc == swedg.ERR_ARG and "32-bit" in msg
+
+
+def test_create_rejects_bad_parameters():
+    bad = [swedg.Params(2, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 0),   # flux
+           swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 2, 0.5, 0),   # rk
+           swedg.Params(1, 1, -1.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 0),  # eps0
+           swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, -1.0, 0, 0.5, 0),           # h_tol
+           swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 3)]   # volume
+    for p in bad:
+        rc, _ = _call_create(3, 1, p)
+        assert rc == swedg.ERR_ARG
+
+
+def test_ensemble_create_rejects_empty_and_bad_members():
+    lib = swedg.lib()
+    p = swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 0)
+    h = ctypes.c_void_p()
+    assert lib.swe_ens_create(0, None, 9.81, ctypes.byref(p), ctypes.byref(h)) == swedg.ERR_ARG
+    arr = (swedg.Instance * 1)()
+    arr[0] = swedg.Instance(3, 0, None, None, None, None, None, None)  # K = 0
+    assert lib.swe_ens_create(1, arr, 9.81, ctypes.byref(p), ctypes.byref(h)) == swedg.ERR_ARG
+
+
+def test_null_contexts_are_rejected():
+    lib = swedg.lib()
+    assert lib.swe_rhs(None, None, None, None) == swedg.ERR_ARG
+    assert lib.swe_step(None, None, 0.0, 1, None, None) == swedg.ERR_ARG
+    assert lib.swe_rhs_adjoint(None, None, None, None, None, None) == swedg.ERR_ARG
+    assert lib.swe_gauge_misfit(None, None, 0, None, None, None, None, None, None, None) == swedg.ERR_ARG
+    lib.swe_destroy(None)
+    lib.swe_ens_destroy(None)
