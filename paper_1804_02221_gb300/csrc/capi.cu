@@ -238,9 +238,9 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
                         const long long nb = (long long)k * nn + (d == 0 ? l * n + q : q * n + l);
                         const int ii = d == 0 ? i : l, jj = d == 0 ? l : i;
                         const double s = w[ii] * w[jj] * D[i * n + q] * 0.25;
-                        const size_t base = ((((size_t)k * 2 + d) * NP + pr) * 2) * n + l;
+                        const size_t base = ((((size_t)k * 2 + d) * NP + pr) * n + l) * 2;
                         pm[base] = s * (vx[na] + vx[nb]);
-                        pm[base + n] = s * (vy[na] + vy[nb]);
+                        pm[base + 1] = s * (vy[na] + vy[nb]);
                     }
             }
         }
@@ -337,6 +337,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     m.KN = KN;
     m.KS = KS;
     m.g = g;
+    m.r2g = 0.5 / g;
     cudaError_t e2 = cudaSuccess;
 #define UP(dst, src)                                  \
     dst = dev_upload(c, src, e2);                     \

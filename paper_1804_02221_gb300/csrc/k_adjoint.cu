@@ -75,7 +75,8 @@ __device__ __forceinline__ void pair_loop_adj(const double* __restrict__ s, int 
         for (int q = i + 1; q < n; ++q) {
             const int nq = base + q * stride;
             const int pr = pair_index_adj<N>(i, q);
-            const double sx = __ldg(pmk + (2 * pr) * n), sy = __ldg(pmk + (2 * pr + 1) * n);
+            const double2 c = __ldg(reinterpret_cast<const double2*>(pmk + 2 * pr * n));
+            const double sx = c.x, sy = c.y;
             const double d1 = a1 - sA1[nq], d2 = a2 - sA2[nq], d3 = a3 - sA3[nq];
             const double Q = fma(hu_i + sHU[nq], sx, (hv_i + sHV[nq]) * sy);
             const double Qb = fma(v_i + sV[nq], d3, fma(u_i + sU[nq], d2, 2.0 * d1));
@@ -153,8 +154,8 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
     const int e = t / n, l = t - e * n;
     const long long k = k0 + e;
     const bool valid = k < m.K;
-    const double* pmx = m.pm + ((size_t)(valid ? k : 0) * 2 * NP * 2) * n + l;
-    const double* pme = pmx + (size_t)NP * 2 * n;
+    const double* pmx = m.pm + ((size_t)(valid ? k : 0) * 2 * NP * n + l) * 2;
+    const double* pme = pmx + (size_t)NP * n * 2;
     const double g2 = 2.0 * m.g;
     double gH[n], gHU[n], gHV[n], gU[n], gV[n];
 #pragma unroll
@@ -440,8 +441,8 @@ __global__ void __launch_bounds__(32 * AVA_WPB) k_av_adj(AvAdjArgs a) {
 __device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
 
 template <bool ES>
-__device__ __forceinline__ void normal_flux_adj(double g, double hm, double hp, double utm, double utp, double vtm,
-                                                double vtp, double bm, double bp, double F1b, double F2b,
+__device__ __forceinline__ void normal_flux_adj(double g, double r2g, double hm, double hp, double utm, double utp,
+                                                double vtm, double vtp, double bm, double bp, double F1b, double F2b,
                                                 double F3b, double& hmb, double& hpb, double& utmb, double& utpb,
                                                 double& vtmb, double& vtpb, double& bmb, double& bpb) {
     const double ha = 0.5 * (hm + hp), ua = 0.5 * (utm + utp), va = 0.5 * (vtm + vtp);
@@ -452,7 +453,6 @@ __device__ __forceinline__ void normal_flux_adj(double g, double hm, double hp, 
         const double ca = 0.5 * (cm + cp);
         const double gH = g * ((hp + bp) - (hm + bm));
         const double dut = utp - utm, dvt = vtp - vtm;
-        const double r2g = 0.5 / g;
         const double A1 = fabs(ua + ca) * r2g, B1 = fma(ca, dut, gH);
         const double A3 = fabs(ua - ca) * r2g, B3 = fma(-ca, dut, gH);
         const double s1 = A1 * B1, s3 = A3 * B3, d1 = s1 + s3;
@@ -523,7 +523,7 @@ __global__ void k_surface_adj(DeviceMesh m, const double* __restrict__ W, const 
         const double G1b = Gfo[tm] - Gfo[tp], G2b = Gfo[S + tm] - Gfo[S + tp], G3b = Gfo[2 * S + tm] - Gfo[2 * S + tp];
         const double F1b = js * G1b, F2b = js * fma(nx, G2b, ny * G3b), F3b = js * fma(-ny, G2b, nx * G3b);
         double hmb, hpb, utmb, utpb, vtmb, vtpb, bmb, bpb;
-        normal_flux_adj<ES>(g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1b, F2b, F3b, hmb, hpb, utmb,
+        normal_flux_adj<ES>(g, m.r2g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1b, F2b, F3b, hmb, hpb, utmb,
                             utpb, vtmb, vtpb, bmb, bpb);
         // rotation: ut = nx u + ny v, vt = nx v - ny u
         double umb = fma(nx, utmb, -ny * vtmb), vmb = fma(ny, utmb, nx * vtmb);
@@ -563,7 +563,7 @@ __global__ void k_wall_adj(DeviceMesh m, const double* __restrict__ W, const dou
         const double G1b = Gfo[tm], G2b = Gfo[S + tm], G3b = Gfo[2 * S + tm];
         const double F1b = js * G1b, F2b = js * fma(nx, G2b, ny * G3b), F3b = js * fma(-ny, G2b, nx * G3b);
         double hmb, hpb, utmb, utpb, vtmb, vtpb, bmb, bpb;
-        normal_flux_adj<ES>(g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1b, F2b, F3b, hmb, hpb, utmb, utpb, vtmb,
+        normal_flux_adj<ES>(g, m.r2g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1b, F2b, F3b, hmb, hpb, utmb, utpb, vtmb,
                             vtpb, bmb, bpb);
         // mirror: hp = hm, utp = -utm, vtp = vtm, bp = bm
         const double hb = hmb + hpb, utb = utmb - utpb, vtb = vtmb + vtpb;

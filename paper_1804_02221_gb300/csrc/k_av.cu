@@ -112,14 +112,13 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
         for (int s = lane; s < AV_EPW * P4; s += 32) {
             const int e = s / P4, L = s - e * P4, t = L / n, p = L - t * n;
             const double* vr = sVi + (t < 2 ? N : N - 1) * n;
+            // t even: sum over i at j = p; t odd: sum over j at i = p. One
+            // code path with an index stride, so that the lanes of a warp do
+            // not split into two half-empty FP64 instruction streams.
+            const int b0 = (t & 1) ? p : p * n, st = (t & 1) ? n : 1;
             double v = 0.0;
-            if ((t & 1) == 0) {
 #pragma unroll
-                for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][p * n + q], v);  // sum over i, j = p
-            } else {
-#pragma unroll
-                for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][q * n + p], v);  // sum over j, i = p
-            }
+            for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][b0 + q * st], v);
             sP[w][e][L] = v;
         }
         // ---- sum w w Q^2: four lanes per element ---------------------------

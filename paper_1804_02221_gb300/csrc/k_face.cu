@@ -38,8 +38,8 @@ __global__ void k_prim(long long KN, const double* __restrict__ W, double* __res
 // ---------------------------------------------------------------------------
 // Flux in the normal frame from the rotated traces (u~, v~) of both sides.
 template <bool ES>
-__device__ __forceinline__ void normal_flux(double g, double hm, double hp, double utm, double utp, double vtm,
-                                            double vtp, double bm, double bp, double& F1, double& F2,
+__device__ __forceinline__ void normal_flux(double g, double r2g, double hm, double hp, double utm, double utp,
+                                            double vtm, double vtp, double bm, double bp, double& F1, double& F2,
                                             double& F3) {
     const double ha = 0.5 * (hm + hp), ua = 0.5 * (utm + utp), va = 0.5 * (vtm + vtp);
     const double h2a = 0.5 * fma(hm, hm, hp * hp);
@@ -50,7 +50,6 @@ __device__ __forceinline__ void normal_flux(double g, double hm, double hp, doub
         const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
         const double gH = g * ((hp + bp) - (hm + bm));
         const double dut = utp - utm, dvt = vtp - vtm;
-        const double r2g = 0.5 / g;
         const double s1 = fabs(ua + ca) * r2g * fma(ca, dut, gH);
         const double s3 = fabs(ua - ca) * r2g * fma(-ca, dut, gH);
         const double d1 = s1 + s3;
@@ -75,7 +74,7 @@ __global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const doub
         const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
         const double utp = fma(nx, up, ny * vp), vtp = fma(nx, vp, -ny * up);
         double F1, F2, F3;
-        normal_flux<ES>(g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1, F2, F3);
+        normal_flux<ES>(g, m.r2g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1, F2, F3);
         const double G1 = js * F1;
         const double G2 = js * fma(nx, F2, -ny * F3);
         const double G3 = js * fma(ny, F2, nx * F3);
@@ -110,7 +109,7 @@ __global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double*
         const double hm = W[im], um = uv[im], vm = uv[m.KN + im], bm = m.bn[im];
         const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
         double F1, F2, F3;
-        normal_flux<ES>(g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1, F2, F3);
+        normal_flux<ES>(g, m.r2g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1, F2, F3);
         Fout[tm] = js * F1;
         Fout[m.KS + tm] = js * fma(nx, F2, -ny * F3);
         Fout[2 * m.KS + tm] = js * fma(ny, F2, nx * F3);

@@ -13,11 +13,17 @@
 //    and the diagonal of D~ = 2D + S vanishes for LGL nodes.
 //  * The static per-pair factor w_i w_j D_iq / 4 (a_i + a_q) (a the
 //    contravariant vector of the line direction: (y_eta, -x_eta) along xi,
-//    (-y_xi, x_xi) along eta) is precomputed on the host, so one pair costs
+//    (-y_xi, x_xi) along eta) is precomputed on the host and read as one
+//    16-byte (Sx, Sy) load. The pair's fluxes are
 //      Q  = (hu_i+hu_q) Sx + (hv_i+hv_q) Sy,   P = 2g h_i h_q,
 //      X2 = (u_i+u_q) Q + P Sx,                X3 = (v_i+v_q) Q + P Sy,
-//    contributions (2Q, X2, X3) to node i and their negatives to node q:
-//    17 FP64 instructions.
+//    with contributions (2Q, X2, X3) to node i and their negatives to node
+//    q. The own-velocity parts u_i Q (node i) and u_q Q (node q) are not
+//    formed per pair: each node accumulates A1 = sum of +-Q and, per pair,
+//    only the partner's velocity term, u_q Q + P Sx at node i and
+//    -(u_i Q + P Sx) at node q; after both lines the node adds u A1 (and
+//    v A1) and doubles A1. One pair is then 15 FP64 instructions (4 for Q,
+//    1 for P, 2 for the mass sums, 8 fused multiply-adds for the momenta).
 //  * One thread per element line: it runs its xi-line, hands the results
 //    through shared memory, then runs the eta-line with the same index
 //    starting from them, and finishes the nodes of that column (interface
@@ -70,13 +76,27 @@ constexpr bool vol_fits() {
     return vol_smem<N, AV, TPB>() <= 227 * 1024;
 }
 
+// Blocks per SM that the shared memory admits (228 KB per SM, 1 KB reserved
+// per block), passed to __launch_bounds__ so that the register allocation
+// does not lower the occupancy below what the staging allows.
+template <int N, bool AV, int TPB>
+constexpr int vol_min_blocks() {
+    constexpr int warps = (vol_ne<N, TPB>() * (N + 1) + 31) / 32;
+    constexpr int by_smem = (int)((228 * 1024) / (vol_smem<N, AV, TPB>() + 1024));
+    constexpr int by_warps = 64 / warps;
+    constexpr int b = by_smem < by_warps ? by_smem : by_warps;
+    return b > 0 ? b : 1;
+}
+
 template <int N>
 __host__ __device__ constexpr int pair_index(int i, int q) {
     return i * (N + 1) - i * (i + 1) / 2 + (q - i - 1);
 }
 
-// All pairs of one line: nodes base + p*stride, p = 0..N; pair constants at
-// pmk[(2*pair + c) * (N+1)].
+// All pairs of one line: nodes base + p*stride, p = 0..N; the (Sx, Sy) pair
+// constants of the thread's line at pmk[2 * pair * (N+1)] (16-byte aligned).
+// Accumulates A1 += +-Q and the partner-velocity parts of the momenta (the
+// own-velocity parts u A1, v A1 are added once per node by the caller).
 template <int N, int BLK>
 __device__ __forceinline__ void pair_loop(const double* __restrict__ s, int base, int stride,
                                           const double* __restrict__ pmk, double* A1, double* A2,
@@ -96,23 +116,22 @@ __device__ __forceinline__ void pair_loop(const double* __restrict__ s, int base
         for (int q = i + 1; q < n; ++q) {
             const int nq = base + q * stride;
             const int pr = pair_index<N>(i, q);
-            const double sx = __ldg(pmk + (2 * pr) * n), sy = __ldg(pmk + (2 * pr + 1) * n);
-            const double Q = fma(hu_i + sHU[nq], sx, (hv_i + sHV[nq]) * sy);
+            const double2 c = __ldg(reinterpret_cast<const double2*>(pmk + 2 * pr * n));
+            const double Q = fma(hu_i + sHU[nq], c.x, (hv_i + sHV[nq]) * c.y);
             const double P = p_i * sH[nq];
-            const double X2 = fma(u_i + sU[nq], Q, P * sx);
-            const double X3 = fma(v_i + sV[nq], Q, P * sy);
-            A1[i] = fma(2.0, Q, A1[i]);
-            A1[q] = fma(-2.0, Q, A1[q]);
-            A2[i] += X2;
-            A2[q] -= X2;
-            A3[i] += X3;
-            A3[q] -= X3;
+            A1[i] += Q;
+            A1[q] -= Q;
+            A2[i] = fma(P, c.x, fma(sU[nq], Q, A2[i]));
+            A2[q] = fma(-P, c.x, fma(-u_i, Q, A2[q]));
+            A3[i] = fma(P, c.y, fma(sV[nq], Q, A3[i]));
+            A3[q] = fma(-P, c.y, fma(-v_i, Q, A3[q]));
         }
     }
 }
 
 template <int N, bool AV, int TPB>
-__global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1)) k_volume(VolArgs a) {
+__global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N, AV, TPB>()))
+    k_volume(VolArgs a) {
     constexpr int n = N + 1, nn = n * n, NE = vol_ne<N, TPB>(), NT = NE * n, BLK = NE * nn;
     constexpr int NP = N * (N + 1) / 2;
     extern __shared__ double sm[];
@@ -149,8 +168,8 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1)) k_volume(VolArgs a
     const int e = t / n, l = t - e * n;
     const long long k = k0 + e;
     const bool valid = k < m.K;
-    const double* pmx = m.pm + ((size_t)(valid ? k : 0) * 2 * NP * 2) * n + l;
-    const double* pme = pmx + (size_t)NP * 2 * n;
+    const double* pmx = m.pm + ((size_t)(valid ? k : 0) * 2 * NP * n + l) * 2;
+    const double* pme = pmx + (size_t)NP * n * 2;
     double A1[n], A2[n], A3[n];
 
     // ---- xi-line j = l ----------------------------------------------------
@@ -173,6 +192,15 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1)) k_volume(VolArgs a
         A3[p] = S(F_A3)[e * nn + p * n + l];
     }
     if (valid) pair_loop<N, BLK>(sm, e * nn + l, n, pme, A1, A2, A3);
+    // own-velocity parts of the momentum fluxes, then the mass flux 2 sum Q
+    // (before the viscous staging reuses the velocity planes)
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        const int nd = e * nn + p * n + l;
+        A2[p] = fma(S(F_U)[nd], A1[p], A2[p]);
+        A3[p] = fma(S(F_V)[nd], A1[p], A3[p]);
+        A1[p] += A1[p];
+    }
 
     // ---- viscous fluxes of the block's viscous elements --------------------
     const double ek = (AV && valid) ? a.eps[k] : 0.0;

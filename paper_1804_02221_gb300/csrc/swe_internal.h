@@ -71,6 +71,7 @@ struct DeviceMesh {
     long long KN;       // K*n*n
     long long KS;       // K*4*n
     double g;
+    double r2g;         // 0.5 / g (the interface dissipation's eigenvalue scale)
     // per node
     const double* axx;  // contravariant xi vector (y_eta, -x_eta)
     const double* axy;
@@ -85,8 +86,9 @@ struct DeviceMesh {
     const double* nae;  // |a_eta| / J
     const double* rvol; // [K] 1 / sum_ij w_i w_j J
     const double* fwJ;  // -1 / (w_i w_j J)
-    // Pair constants of the volume kernel, [K][2 directions][N(N+1)/2 pairs][2][n lines]:
-    // w_i w_j D_iq / 4 * (a_i + a_q) for the pair (i, q), i < q, of each line.
+    // Pair constants of the volume kernel, [K][2 directions][N(N+1)/2 pairs][n lines][2]:
+    // w_i w_j D_iq / 4 * (a_i + a_q) for the pair (i, q), i < q, of each line; the
+    // two components of a line are adjacent (one 16-byte load).
     const double* pm;
     // per unique face node
     const int32_t* f_im;   // owner node id (k*n*n + j*n + i)
