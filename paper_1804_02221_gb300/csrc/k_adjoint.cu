@@ -635,7 +635,7 @@ __global__ void __launch_bounds__(32 * GA_WPB) k_gather_adj(GatherArgs a) {
             double ghu = a.Ga[KN + gid], ghv = a.Ga[2 * KN + gid];
             const double h = a.W[gid];
             if (h > 0.0) {
-                const double rh = 1.0 / h;
+                const double rh = recip_pos(h);
                 gh -= (a.uv[gid] * gu + a.uv[KN + gid] * gv) * rh;
                 ghu = fma(gu, rh, ghu);
                 ghv = fma(gv, rh, ghv);
@@ -902,9 +902,10 @@ __global__ void __launch_bounds__(128) k_limit_rec(LimRecArgs a) {
             a.W[gid] = h[r];
             a.W[KN + gid] = hu[r];
             a.W[2 * KN + gid] = hv[r];
-            const double rh = (long long)__double_as_longlong(h[r]) > 0 ? 1.0 / h[r] : 0.0;
-            a.uv[gid] = hu[r] * rh;
-            a.uv[KN + gid] = hv[r] * rh;
+            double u, v;
+            velocities(h[r], hu[r], hv[r], u, v);
+            a.uv[gid] = u;
+            a.uv[KN + gid] = v;
         }
     }
 }

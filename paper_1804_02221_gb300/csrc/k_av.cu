@@ -190,7 +190,9 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
             }
         }
         __syncwarp();
-#pragma unroll
+        // not unrolled: the viscous elements are few, and the unrolled loop
+        // doubled the kernel's registers and halved its occupancy
+#pragma unroll 1
         for (int r = 0; r < PER; ++r) {
             const int node = lane + 32 * r;
             if (node >= nn) continue;

@@ -18,10 +18,10 @@ __global__ void k_prim(long long KN, const double* __restrict__ W, double* __res
     if (stopped(stop)) return;
     for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < KN;
          id += (long long)gridDim.x * blockDim.x) {
-        const double h = W[id];
-        const double rh = h > 0.0 ? 1.0 / h : 0.0;
-        uv[id] = W[KN + id] * rh;
-        uv[KN + id] = W[2 * KN + id] * rh;
+        double u, v;
+        velocities(W[id], W[KN + id], W[2 * KN + id], u, v);
+        uv[id] = u;
+        uv[KN + id] = v;
     }
 }
 
@@ -299,9 +299,10 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, in
             a.W[KN + gid] = hu[r];
             a.W[2 * KN + gid] = hv[r];
             if (a.uv) {
-                const double rh = (long long)__double_as_longlong(h[r]) > 0 ? 1.0 / h[r] : 0.0;
-                a.uv[gid] = hu[r] * rh;
-                a.uv[KN + gid] = hv[r] * rh;
+                double u, v;
+                velocities(h[r], hu[r], hv[r], u, v);
+                a.uv[gid] = u;
+                a.uv[KN + gid] = v;
             }
         }
     }
@@ -371,7 +372,7 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
         const double i1 = fma(2.0, ua, A) * rwa;
         if (i1 > 0.0) inv = fmax(inv, i1);
         const double jump = utp - utm;
-        if (hm > 0.0 && B * jump < 0.0) inv = fmax(inv, fabs(ca * B * jump) * rwa / (g * hm));
+        if (hm > 0.0 && B * jump < 0.0) inv = fmax(inv, fabs(ca * B * jump) * rwa * recip_pos(g * hm));
     }
     inv = warp_max(inv);
     if (lane == 0 && inv > 0.0) atomic_max_pos(&bits[1], inv);
@@ -431,7 +432,7 @@ __global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int wh
             s2 = fma(wj, hv, s2);
         }
         if (what != 0) {
-            const double kin = h > 0.0 ? 0.5 * fma(hu, hu, hv * hv) / h : 0.0;
+            const double kin = kinetic(h, hu, hv);
             const double e = kin + g * h * fma(0.5, h, m.bn[id]);
             s3 = fma(wj, e, s3);
         }
@@ -474,7 +475,7 @@ __global__ void k_reduce_inst(DeviceMesh m, const double* __restrict__ W, const 
         s0 = fma(wj, h, s0);
         s1 = fma(wj, hu, s1);
         s2 = fma(wj, hv, s2);
-        const double kin = h > 0.0 ? 0.5 * fma(hu, hu, hv * hv) / h : 0.0;
+        const double kin = kinetic(h, hu, hv);
         s3 = fma(wj, kin + g * h * fma(0.5, h, m.bn[id]), s3);
     }
     sh[0][threadIdx.x] = s0;

@@ -88,6 +88,12 @@ constexpr int vol_min_blocks() {
     return b > 0 ? b : 1;
 }
 
+// x != 0 (either sign of zero counts as zero), from the bit pattern: an
+// integer test, so that it costs no FP64 instruction.
+__device__ __forceinline__ bool nonzero(double x) {
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ULL;
+}
+
 template <int N>
 __host__ __device__ constexpr int pair_index(int i, int q) {
     return i * (N + 1) - i * (i + 1) / 2 + (q - i - 1);
@@ -170,12 +176,48 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     const bool valid = k < m.K;
     const double* pmx = m.pm + ((size_t)(valid ? k : 0) * 2 * NP * n + l) * 2;
     const double* pme = pmx + (size_t)NP * n * 2;
+    const long long KS = m.KS;
+    const long long side = (valid ? k : 0) * 4 * n;
+    const double ek = (AV && valid) ? a.eps[k] : 0.0;
+    const bool visc = ek > 0.0;
     double A1[n], A2[n], A3[n];
 
     // ---- xi-line j = l ----------------------------------------------------
 #pragma unroll
     for (int p = 0; p < n; ++p) A1[p] = A2[p] = A3[p] = 0.0;
-    if (valid) pair_loop<N, BLK>(sm, e * nn + l * n, 1, pmx, A1, A2, A3);
+    if (valid) {
+        pair_loop<N, BLK>(sm, e * nn + l * n, 1, pmx, A1, A2, A3);
+        // Lifts at the row's end nodes i = N (side 1) and i = 0 (side 3),
+        // weighted by the tangential LGL weight w_l: done here, where every
+        // lane holds one of them, rather than in the column phase where only
+        // two lanes of eight would. A1 still holds sum Q there (doubled and
+        // multiplied by u, v later), so it gets half the mass lift and the
+        // momenta get -u, -v times that half in advance.
+        const double wl = wq<N>(l), wlh = 0.5 * wl;
+        const long long gid0 = k * nn + l * n;
+#pragma unroll
+        for (int end = 0; end < 2; ++end) {
+            const int p = end == 0 ? N : 0, f = end == 0 ? 1 : 3;
+            const long long sl = side + f * n + l;
+            const int nd = e * nn + l * n + p;
+            const double t1 = wlh * a.Fout[sl];
+            A1[p] += t1;
+            A2[p] = fma(-S(F_U)[nd], t1, fma(wl, a.Fout[KS + sl], A2[p]));
+            A3[p] = fma(-S(F_V)[nd], t1, fma(wl, a.Fout[2 * KS + sl], A3[p]));
+            if (AV) {
+                // viscous lift -w_l (F^v*_out - own outward flux); skipped
+                // where no viscous flux reaches the face (both sides inviscid)
+                const double fv2 = a.Fvout[sl], fv3 = a.Fvout[KS + sl];
+                if (visc || nonzero(fv2) || nonzero(fv3)) {
+                    const double sg = end == 0 ? 1.0 : -1.0;
+                    const double own2 = visc ? sg * a.Fvt[gid0 + p] : 0.0;
+                    const double own3 = visc ? sg * a.Fvt[m.KN + gid0 + p] : 0.0;
+                    A2[p] = fma(-wl, fv2 - own2, A2[p]);
+                    A3[p] = fma(-wl, fv3 - own3, A3[p]);
+                }
+            }
+        }
+    }
 #pragma unroll
     for (int p = 0; p < n; ++p) {
         S(F_A1)[e * nn + l * n + p] = A1[p];
@@ -203,9 +245,8 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     }
 
     // ---- viscous fluxes of the block's viscous elements --------------------
-    const double ek = (AV && valid) ? a.eps[k] : 0.0;
     if (AV) {
-        const int any = __syncthreads_or(ek > 0.0);
+        const int any = __syncthreads_or(visc);
         if (any) {
             for (int idx = t; idx < BLK; idx += NT) {
                 const int ee = idx / nn;
@@ -226,14 +267,11 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
 
     // ---- nodes (i = l, j = p): lifts, viscous terms, source, scaling --------
     const int i = l;
-    const double wi = c_w[vec_offset(N) + i];
-    const long long KS = m.KS;
-    const long long side = k * 4 * n;
+    const double wi = wq<N>(i);
     const int eb = e * nn;
 #pragma unroll
     for (int p = 0; p < n; ++p) {
         const int j = p;
-        const double wj = wq<N>(j);
         const long long gid = k * nn + j * n + i;
         double a1 = A1[p], a2 = A2[p], a3 = A3[p];
         // interface flux: w_i w_j (1/w_0) F_out = (tangential weight) F_out
@@ -245,10 +283,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         };
         if (j == 0) lift(0, i, wi);
         if (j == N) lift(2, i, wi);
-        if (i == N) lift(1, j, wj);
-        if (i == 0) lift(3, j, wj);
         if (AV) {
-            const bool visc = ek > 0.0;
             const int nd = eb + j * n + i;
             if (visc) {
                 double L2 = 0.0, L3 = 0.0;
@@ -260,22 +295,23 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
                     L2 = fma(dj, S(F_GT2)[eb + q * n + i], L2);
                     L3 = fma(dj, S(F_GT3)[eb + q * n + i], L3);
                 }
-                const double wij = wi * wj;
+                const double wij = wi * wq<N>(j);
                 a2 = fma(-wij, L2, a2);
                 a3 = fma(-wij, L3, a3);
             }
-            const double ft2 = visc ? S(F_FT2)[nd] : 0.0, ft3 = visc ? S(F_FT3)[nd] : 0.0;
-            const double gt2 = visc ? S(F_GT2)[nd] : 0.0, gt3 = visc ? S(F_GT3)[nd] : 0.0;
-            // viscous lift: -(tangential weight) (F^v*_out - own outward flux)
-            auto vlift = [&](int f, int pn, double wt, double own2, double own3) {
-                const long long sl = side + f * n + pn;
-                a2 = fma(-wt, a.Fvout[sl] - own2, a2);
-                a3 = fma(-wt, a.Fvout[KS + sl] - own3, a3);
+            // viscous lift at sides 0 and 2: -(tangential weight) (F^v*_out -
+            // own outward flux), skipped where no viscous flux reaches the face
+            auto vlift = [&](int f, double sg) {
+                const long long sl = side + f * n + i;
+                const double fv2 = a.Fvout[sl], fv3 = a.Fvout[KS + sl];
+                if (visc || nonzero(fv2) || nonzero(fv3)) {
+                    const double own2 = visc ? sg * S(F_GT2)[nd] : 0.0, own3 = visc ? sg * S(F_GT3)[nd] : 0.0;
+                    a2 = fma(-wi, fv2 - own2, a2);
+                    a3 = fma(-wi, fv3 - own3, a3);
+                }
             };
-            if (j == 0) vlift(0, i, wi, -gt2, -gt3);
-            if (j == N) vlift(2, i, wi, gt2, gt3);
-            if (i == N) vlift(1, j, wj, ft2, ft3);
-            if (i == 0) vlift(3, j, wj, -ft2, -ft3);
+            if (j == 0) vlift(0, -1.0);
+            if (j == N) vlift(2, 1.0);
         }
         const double f = m.fwJ[gid];
         const double h = S(F_H)[eb + j * n + i];

@@ -33,6 +33,53 @@ __device__ __forceinline__ double wq(int i) {
     return c_w[vec_offset(N) + i];
 }
 
+// 1/x for normal x in [2^-1022, 2^1022): the hardware's approximate
+// reciprocal (PTX rcp.approx.ftz.f64) refined by two steps of Newton's
+// iteration for f(r) = 1/r - x, r <- r + r (1 - x r), each of which squares
+// the relative error; the result is within one unit in the last place of 1/x
+// (four FP64 fused multiply-adds instead of a correctly rounded division).
+__device__ __forceinline__ double recip_normal(double x) {
+    double r;
+    asm("rcp.approx.ftz.f64 %0, %1;" : "=d"(r) : "d"(x));
+    double e = fma(-x, r, 1.0);
+    r = fma(r, e, r);
+    e = fma(-x, r, 1.0);
+    return fma(r, e, r);
+}
+
+// x in the range of recip_normal (an integer test of the bit pattern; false
+// for zero, negative, subnormal, huge, infinite and NaN x).
+__device__ __forceinline__ bool recip_range(double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return b - 0x0010000000000000ULL < 0x7fd0000000000000ULL - 0x0010000000000000ULL;
+}
+
+// 1/x for x > 0 (the division outside the range of recip_normal).
+__device__ __forceinline__ double recip_pos(double x) {
+    return recip_range(x) ? recip_normal(x) : 1.0 / x;
+}
+
+// Velocities u = hu/h, v = hv/h where h > 0, zero where h <= 0.
+__device__ __forceinline__ void velocities(double h, double hu, double hv, double& u, double& v) {
+    if (recip_range(h)) {
+        const double r = recip_normal(h);
+        u = hu * r;
+        v = hv * r;
+    } else if ((long long)__double_as_longlong(h) > 0) {
+        u = hu / h;  // subnormal, huge, infinite or NaN h
+        v = hv / h;
+    } else {
+        u = v = 0.0;
+    }
+}
+
+// Kinetic energy (hu^2 + hv^2)/(2h) where h > 0, zero where h <= 0.
+__device__ __forceinline__ double kinetic(double h, double hu, double hv) {
+    const double s = 0.5 * fma(hu, hu, hv * hv);
+    if (recip_range(h)) return s * recip_normal(h);
+    return (long long)__double_as_longlong(h) > 0 ? s / h : 0.0;
+}
+
 __device__ __forceinline__ bool stopped(const int* stop) {
     return stop != nullptr && *(volatile const int*)stop != 0;
 }

@@ -160,6 +160,33 @@ def test_mass_entropy_parity(N):
     assert np.array_equal(both[:3], mg) and both[3] == eg
 
 
+def test_entropy_and_velocities_wide_range_of_heights():
+    """1/h is a refined hardware reciprocal on the GPU (and the division for
+    subnormal h): the kinetic energy and the velocities must hold over water
+    heights from 1e-300 to 1e3, including subnormal and dry nodes, against
+    the oracle's plain division."""
+    p = I.random_rough(N=3, K1=6, seed=11, rotate_seed=1)
+    rng = np.random.default_rng(12)
+    W = p.W.copy()
+    h = 10.0 ** rng.uniform(-300, 3, size=W[0].shape)
+    flat = h.reshape(-1)
+    flat[::97] = 0.0
+    flat[1::97] = 5e-320          # subnormal
+    flat[2::97] = 2.0 ** -1021    # normal, near the bottom of the range
+    W[0] = h
+    W[1] = np.where(h > 1e-100, rng.uniform(-1, 1, size=h.shape) * h, 0.0)
+    W[2] = np.where(h > 1e-100, rng.uniform(-1, 1, size=h.shape) * h, 0.0)
+    o, g = pair(p)
+    eo, eg = o.entropy(W), g.entropy(dev(W))
+    assert abs(eg - eo) < 1e-13 * abs(eo)
+    # velocities enter the right-hand side: EC flux on a flat-bottom-free
+    # state is finite and matches the oracle
+    Ro = o.rhs(W)
+    Rg = g.rhs(dev(W)).cpu().numpy()
+    assert np.isfinite(Rg).all()
+    assert rhs_err(Rg, Ro, p, W) < RHS_TOL
+
+
 def test_step_parity_lake_hump_100_lsrk():
     """Lake at rest plus hump, N=3, 8x8 curved periodic quads, ES flux, AV,
     limiter, 100 LSRK4(5) steps at CFL 0.5: relative 1e-10."""
