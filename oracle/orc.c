@@ -36,6 +36,12 @@
  *    -g h J b_x, -g h J b_y with J b_x = y_eta b_xi - y_xi b_eta,
  *    J b_y = -x_eta b_xi + x_xi b_eta (the continuous limit of the split
  *    source).
+ *
+ * Pins: every function is checked by the CPU tests against closed forms,
+ * identities or brute force, except one sub-case: the solid-wall term of
+ * the positivity time step in orc_max_dt (mirror state at a wall face) is
+ * parity unpinned (a wall carries no mass flux, so positivity cannot
+ * observe it; it is exercised only by GPU parity).
  */
 #include "orc.h"
 

@@ -247,7 +247,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
 
     // ---- unique faces and element sides ----
     std::vector<int32_t> f_im, f_ip, f_tm, f_tp, s_nb(KS), w_im, w_tm;
-    std::vector<double> f_nx, f_ny, f_js, f_bm, f_bp, s_nx(KS), s_ny(KS), s_rwa(KS), w_nx, w_ny, w_js;
+    std::vector<double> f_nx, f_ny, f_js, f_sx, f_sy, f_bm, f_bp, s_nx(KS), s_ny(KS), s_rwa(KS), w_nx, w_ny, w_js;
     const double w0 = w[0];
     auto outward = [&](int k, int f, int i, int j, double& nx, double& ny) {
         const long long id = (long long)k * nn + j * n + i;
@@ -307,6 +307,8 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
                     f_nx.push_back(nx / js);
                     f_ny.push_back(ny / js);
                     f_js.push_back(js);
+                    f_sx.push_back(nx);
+                    f_sy.push_back(ny);
                     f_bm.push_back(bn[own]);
                     f_bp.push_back(bn[nb]);
                 }
@@ -338,6 +340,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     m.KS = KS;
     m.g = g;
     m.r2g = 0.5 / g;
+    m.g4 = 0.25 * g;
     cudaError_t e2 = cudaSuccess;
 #define UP(dst, src)                                  \
     dst = dev_upload(c, src, e2);                     \
@@ -346,7 +349,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     UP(m.srcx, srcx) UP(m.srcy, srcy) UP(m.bn, bn) UP(m.nax, cfln) UP(m.rvol, rvol)
     UP(m.fwJ, fwJ) UP(m.pm, pm)
     UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
-    UP(m.f_ny, f_ny) UP(m.f_js, f_js) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
+    UP(m.f_ny, f_ny) UP(m.f_js, f_js) UP(m.f_sx, f_sx) UP(m.f_sy, f_sy) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
     UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
     UP(m.w_im, w_im) UP(m.w_tm, w_tm) UP(m.w_nx, w_nx) UP(m.w_ny, w_ny) UP(m.w_js, w_js)
 #undef UP

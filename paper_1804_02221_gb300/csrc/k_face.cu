@@ -36,26 +36,33 @@ __global__ void k_prim(long long KN, const double* __restrict__ W, double* __res
 // g[[h+b]] - {c}[[u~]]). Writes +F to the owner's side slot and -F to the
 // neighbour's, and the BR1 interface values {u}, {v} to both.
 // ---------------------------------------------------------------------------
-// Flux in the normal frame from the rotated traces (u~, v~) of both sides.
+// Flux in the normal frame from the rotated traces (u~, v~) of both sides;
+// g4 = g/4 and r2g = 1/(2g) are the context's constants. With
+// c_a = {c} = c4m + c4p, c4 = sqrt(g4 max(h, 0)) = c/2, the half-weighted
+// projections of the dissipation are
+//   s1 = |{u~} + {c}| (({c}/(2g)) [[u~]] + [[h+b]]/2),
+//   s3 = |{u~} - {c}| (-({c}/(2g)) [[u~]] + [[h+b]]/2),
+// and the EC flux's pressure term g {h^2}/2 = g4 (h-^2 + h+^2).
 template <bool ES>
-__device__ __forceinline__ void normal_flux(double g, double r2g, double hm, double hp, double utm, double utp,
+__device__ __forceinline__ void normal_flux(double g4, double r2g, double hm, double hp, double utm, double utp,
                                             double vtm, double vtp, double bm, double bp, double& F1, double& F2,
                                             double& F3) {
     const double ha = 0.5 * (hm + hp), ua = 0.5 * (utm + utp), va = 0.5 * (vtm + vtp);
-    const double h2a = 0.5 * fma(hm, hm, hp * hp);
-    F1 = ha * ua;
-    F2 = fma(F1, ua, 0.5 * g * h2a);
-    F3 = F1 * va;
+    const double F1ec = ha * ua;
+    F1 = F1ec;
+    F2 = fma(F1ec, ua, g4 * fma(hm, hm, hp * hp));
+    F3 = F1ec * va;
     if (ES) {
-        const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
-        const double gH = g * ((hp + bp) - (hm + bm));
+        const double ca = sqrt_pos(g4 * pos_part(hm)) + sqrt_pos(g4 * pos_part(hp));
+        const double jH = 0.5 * ((hp + bp) - (hm + bm));
+        const double cr = ca * r2g;
         const double dut = utp - utm, dvt = vtp - vtm;
-        const double s1 = fabs(ua + ca) * r2g * fma(ca, dut, gH);
-        const double s3 = fabs(ua - ca) * r2g * fma(-ca, dut, gH);
+        const double s1 = fabs(ua + ca) * fma(cr, dut, jH);
+        const double s3 = fabs(ua - ca) * fma(-cr, dut, jH);
         const double d1 = s1 + s3;
         F1 = fma(-0.5, d1, F1);
         F2 = fma(-0.5, fma(ua, d1, ca * (s1 - s3)), F2);
-        F3 = fma(-0.5, fma(va, d1, fabs(ha * ua) * dvt), F3);
+        F3 = fma(-0.5, fma(va, d1, fabs(F1ec) * dvt), F3);
     }
 }
 
@@ -64,26 +71,27 @@ __global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const doub
                           double* __restrict__ Fout, double* __restrict__ Ustar, const int* stop) {
     if (stopped(stop)) return;
     const long long total = (long long)m.nfaces * m.n;
-    const double g = m.g;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long im = m.f_im[t], ip = m.f_ip[t], tm = m.f_tm[t], tp = m.f_tp[t];
-        const double nx = m.f_nx[t], ny = m.f_ny[t], js = m.f_js[t];
+        const double nx = m.f_nx[t], ny = m.f_ny[t];
         const double hm = W[im], hp = W[ip];
         const double um = uv[im], vm = uv[m.KN + im], up = uv[ip], vp = uv[m.KN + ip];
         const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
         const double utp = fma(nx, up, ny * vp), vtp = fma(nx, vp, -ny * up);
         double F1, F2, F3;
-        normal_flux<ES>(g, m.r2g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1, F2, F3);
-        const double G1 = js * F1;
-        const double G2 = js * fma(nx, F2, -ny * F3);
-        const double G3 = js * fma(ny, F2, nx * F3);
+        normal_flux<ES>(m.g4, m.r2g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1, F2, F3);
+        // rotate back with the unscaled normal (the surface Jacobian included)
+        const double sx = m.f_sx[t], sy = m.f_sy[t];
+        const double G1 = m.f_js[t] * F1;
+        const double G2 = fma(sx, F2, -sy * F3);
+        const double G3 = fma(sy, F2, sx * F3);
         Fout[tm] = G1;
         Fout[m.KS + tm] = G2;
         Fout[2 * m.KS + tm] = G3;
-        Fout[tp] = -G1;
-        Fout[m.KS + tp] = -G2;
-        Fout[2 * m.KS + tp] = -G3;
+        Fout[tp] = negated(G1);
+        Fout[m.KS + tp] = negated(G2);
+        Fout[2 * m.KS + tp] = negated(G3);
         const double us = 0.5 * (um + up), vs = 0.5 * (vm + vp);
         Ustar[tm] = us;
         Ustar[m.KS + tm] = vs;
@@ -101,7 +109,6 @@ __global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double*
                        double* __restrict__ Fout, double* __restrict__ Ustar, const int* stop) {
     if (stopped(stop)) return;
     const long long total = (long long)m.nwall * m.n;
-    const double g = m.g;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long im = m.w_im[t], tm = m.w_tm[t];
@@ -109,7 +116,7 @@ __global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double*
         const double hm = W[im], um = uv[im], vm = uv[m.KN + im], bm = m.bn[im];
         const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
         double F1, F2, F3;
-        normal_flux<ES>(g, m.r2g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1, F2, F3);
+        normal_flux<ES>(m.g4, m.r2g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1, F2, F3);
         Fout[tm] = js * F1;
         Fout[m.KS + tm] = js * fma(nx, F2, -ny * F3);
         Fout[2 * m.KS + tm] = js * fma(ny, F2, nx * F3);
@@ -129,14 +136,14 @@ __global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, doubl
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long tm = m.f_tm[t], tp = m.f_tp[t];
-        const double nx = m.f_nx[t] * m.f_js[t], ny = m.f_ny[t] * m.f_js[t];
+        const double nx = m.f_sx[t], ny = m.f_sy[t];
         const long long S = m.KS;
         const double a2 = 0.5 * fma(nx, Fvtr[tm] + Fvtr[tp], ny * (Fvtr[2 * S + tm] + Fvtr[2 * S + tp]));
         const double a3 = 0.5 * fma(nx, Fvtr[S + tm] + Fvtr[S + tp], ny * (Fvtr[3 * S + tm] + Fvtr[3 * S + tp]));
         Fvout[tm] = a2;
         Fvout[S + tm] = a3;
-        Fvout[tp] = -a2;
-        Fvout[S + tp] = -a3;
+        Fvout[tp] = negated(a2);
+        Fvout[S + tp] = negated(a3);
     }
 }
 
@@ -343,7 +350,7 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
     for (int node = lane; node < nn; node += 32) {
         const long long id = k * nn + node;
         const double h = a.W[id], u = a.uv[id], v = a.uv[m.KN + id];
-        const double c = sqrt(g * fmax(h, 0.0));
+        const double c = sqrt_pos(g * pos_part(h));
         const double vel = fabs(fma(m.axx[id], u, m.axy[id] * v)) + fabs(fma(m.aex[id], u, m.aey[id] * v));
         lam = fmax(lam, fma(c, a.cfl_n[id], m.rJ[id] * vel));
     }
@@ -366,7 +373,7 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
         const double utm = fma(nx, a.uv[own], ny * a.uv[m.KN + own]);
         const double utp = wall ? -utm : fma(nx, a.uv[nb], ny * a.uv[m.KN + nb]);
         const double ua = 0.5 * (utm + utp);
-        const double ca = 0.5 * (sqrt(g * fmax(hm, 0.0)) + sqrt(g * fmax(hp, 0.0)));
+        const double ca = sqrt_pos(m.g4 * pos_part(hm)) + sqrt_pos(m.g4 * pos_part(hp));
         const double ap = fabs(ua + ca), am = fabs(ua - ca);
         const double A = ap + am, B = ap - am;
         const double i1 = fma(2.0, ua, A) * rwa;

@@ -59,6 +59,33 @@ __device__ __forceinline__ double recip_pos(double x) {
     return recip_range(x) ? recip_normal(x) : 1.0 / x;
 }
 
+// sqrt(x) for x >= 0: for x in the range of recip_normal, the hardware's
+// approximate reciprocal square root (PTX rsqrt.approx.ftz.f64) y, then
+// s = x y and two Newton (Heron) corrections s <- s + (y/2)(x - s^2) with
+// the slope 1/(2 sqrt x) taken from y; the first squares the relative error
+// of y, the second multiplies the remainder by it again, so the result is
+// within one unit in the last place (six FP64 instructions). Zero and
+// values outside that range take the library square root.
+__device__ __forceinline__ double sqrt_pos(double x) {
+    if (!recip_range(x)) return sqrt(x);
+    double y;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y) : "d"(x));
+    const double hy = 0.5 * y;
+    double s = x * y;
+    s = fma(hy, fma(-s, s, x), s);
+    return fma(hy, fma(-s, s, x), s);
+}
+
+// max(x, 0) by the sign bit (an integer test, no FP64 instruction).
+__device__ __forceinline__ double pos_part(double x) {
+    return (long long)__double_as_longlong(x) > 0 ? x : 0.0;
+}
+
+// -x by the sign bit.
+__device__ __forceinline__ double negated(double x) {
+    return __longlong_as_double(__double_as_longlong(x) ^ (long long)0x8000000000000000ULL);
+}
+
 // Velocities u = hu/h, v = hv/h where h > 0, zero where h <= 0.
 __device__ __forceinline__ void velocities(double h, double hu, double hv, double& u, double& v) {
     if (recip_range(h)) {
