@@ -328,6 +328,7 @@ def sweep(args):
                           "node_updates_per_s": RK_STAGES * prob.nodes / (ms * 1e-3),
                           "rhs_node_updates_per_s": rates, "volume_ms": vol,
                           "volume_tflops": achieved, "volume_frac_at_2070MHz": achieved / peak,
+                          "volume_gbs_algorithmic": volume_bytes_per_node(N) * prob.nodes / (vol * 1e-3) / 1e9,
                           "split_vs_standard": cmp}), flush=True)
         ctx.close()
 

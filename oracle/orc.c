@@ -283,6 +283,22 @@ static double deta(const orc_mesh* m, const double* f, int k, int i, int j) {
     return s;
 }
 
+/* D_xi and D_eta of f - c for a constant c (the same derivative, as D
+ * annihilates constants). Used for the coordinates, with c the element's
+ * first node: differencing first keeps the coordinates' magnitude, which can
+ * exceed the element's size by orders of magnitude, out of the sums. */
+static double dxi_rel(const orc_mesh* m, const double* f, double c, int k, int i, int j) {
+    double s = 0.0;
+    for (int q = 0; q < m->n; ++q) s += m->D[i][q] * (f[nid(m, k, q, j)] - c);
+    return s;
+}
+
+static double deta_rel(const orc_mesh* m, const double* f, double c, int k, int i, int j) {
+    double s = 0.0;
+    for (int q = 0; q < m->n; ++q) s += m->D[j][q] * (f[nid(m, k, i, q)] - c);
+    return s;
+}
+
 void orc_destroy(orc_mesh* m) {
     if (!m) return;
     double* arrs[] = {m->x, m->y, m->b, m->x_xi, m->x_eta, m->y_xi, m->y_eta, m->J,
@@ -356,18 +372,21 @@ int orc_create(int N, int K, const double* x, const double* y, const int* EToE,
     m->Ustar = dalloc((size_t)K * NF * n * 2);
     m->Fvstar = dalloc((size_t)K * NF * n * 2);
     m->grad = dalloc(4 * nn);
-    /* metric terms by differentiating the nodal mapping; J by Eq. JacobianDef */
-    for (int k = 0; k < K; ++k)
+    /* metric terms by differentiating the nodal mapping (coordinates taken
+     * relative to the element's first node); J by Eq. JacobianDef */
+    for (int k = 0; k < K; ++k) {
+        const double x0 = m->x[nid(m, k, 0, 0)], y0 = m->y[nid(m, k, 0, 0)];
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 size_t id = nid(m, k, i, j);
-                m->x_xi[id] = dxi(m, m->x, k, i, j);
-                m->x_eta[id] = deta(m, m->x, k, i, j);
-                m->y_xi[id] = dxi(m, m->y, k, i, j);
-                m->y_eta[id] = deta(m, m->y, k, i, j);
+                m->x_xi[id] = dxi_rel(m, m->x, x0, k, i, j);
+                m->x_eta[id] = deta_rel(m, m->x, x0, k, i, j);
+                m->y_xi[id] = dxi_rel(m, m->y, y0, k, i, j);
+                m->y_eta[id] = deta_rel(m, m->y, y0, k, i, j);
                 m->J[id] = m->x_xi[id] * m->y_eta[id] - m->x_eta[id] * m->y_xi[id];
                 if (!(m->J[id] > 0.0)) { orc_destroy(m); return ORC_ERR_GEOM; }
             }
+    }
     /* split-form bathymetry derivatives of Eq. SourceDisc (plain D, see header) */
     double* tmp1 = dalloc(nn);
     double* tmp2 = dalloc(nn);

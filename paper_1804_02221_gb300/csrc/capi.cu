@@ -155,14 +155,19 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         const double* Y = y + (size_t)k * nn;
         const double* Bk = b + (size_t)k * nn;
         double vol = 0.0;
+        // metric terms from coordinates relative to the element's first node
+        // (D annihilates constants): the sums then do not carry the
+        // coordinates' magnitude, which on fine meshes exceeds the element
+        // size by orders of magnitude and would cost digits of the metrics
+        const double X0 = X[0], Y0 = Y[0];
         for (int j = 0; j < n; ++j)
             for (int i = 0; i < n; ++i) {
                 double x_xi = 0, x_eta = 0, y_xi = 0, y_eta = 0;
                 for (int q = 0; q < n; ++q) {
-                    x_xi += D[i * n + q] * X[j * n + q];
-                    y_xi += D[i * n + q] * Y[j * n + q];
-                    x_eta += D[j * n + q] * X[q * n + i];
-                    y_eta += D[j * n + q] * Y[q * n + i];
+                    x_xi += D[i * n + q] * (X[j * n + q] - X0);
+                    y_xi += D[i * n + q] * (Y[j * n + q] - Y0);
+                    x_eta += D[j * n + q] * (X[q * n + i] - X0);
+                    y_eta += D[j * n + q] * (Y[q * n + i] - Y0);
                 }
                 const double J = x_xi * y_eta - x_eta * y_xi;
                 const long long id = (long long)k * nn + j * n + i;
@@ -642,7 +647,7 @@ int ensure_adjoint(swe_ctx* c) {
     if (e != cudaSuccess) return cuda_fail(e, "adjoint: allocation");
     ADJ_AL(A.Ga, 3 * KN) ADJ_AL(A.Guv, 2 * KN) ADJ_AL(A.Gsl, 4 * KS) ADJ_AL(A.Gfo, 3 * KS)
     ADJ_AL(A.GUs, 2 * KS) ADJ_AL(A.Gfvt, 4 * KN) ADJ_AL(A.Gfvo, 2 * KS) ADJ_AL(A.Gfvtr, 4 * KS)
-    ADJ_AL(A.Gsrc, 2 * KN) ADJ_AL(A.Khb, 3 * KN) ADJ_AL(A.Rb, 3 * KN) ADJ_AL(A.Wnb, 3 * KN)
+    ADJ_AL(A.Gsrc, 2 * KN) ADJ_AL(A.Gsrc_acc, 2 * KN) ADJ_AL(A.Khb, 3 * KN) ADJ_AL(A.Rb, 3 * KN) ADJ_AL(A.Wnb, 3 * KN)
     ADJ_AL(A.Ws, 3 * KN) ADJ_AL(A.Xs, S * 3 * KN) ADJ_AL(A.Ys, S * 3 * KN) ADJ_AL(A.Es, S * K)
 #undef ADJ_AL
     void* q = nullptr;
@@ -723,6 +728,9 @@ extern "C" int swe_step_adjoint(swe_ctx* c, const double* W0, double dt, double*
     // ---- reverse sweep ----
     cudaMemsetAsync(A.Khb, 0, n3 * sizeof(double), s);
     if (c->p.rk == 1) cudaMemsetAsync(A.Wnb, 0, n3 * sizeof(double), s);
+    // the stages' source-coefficient cotangents are summed and carried to
+    // bbar once, after the sweep
+    if (bbar) cudaMemsetAsync(A.Gsrc_acc, 0, 2 * KN * sizeof(double), s);
     for (int st = stages - 1; st >= 0; --st) {
         const double a = c->p.rk == 0 ? kLsrkA[st] : ca[st], b = c->p.rk == 0 ? kLsrkB[st] : cb[st];
         swe::launch_update_adjoint(c, c->p.rk == 0 ? 1 : 2, Wbar, A.Ys + st * n3, A.act + st * K, A.amin + st * K,
@@ -730,8 +738,9 @@ extern "C" int swe_step_adjoint(swe_ctx* c, const double* W0, double dt, double*
         const double* X = A.Xs + st * n3;
         cudaMemcpyAsync(c->w.eps, A.Es + st * K, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
         adjoint_prerequisites(c, X, s, true);
-        swe::launch_rhs_adjoint(c, X, A.Rb, Wbar, bbar, s);
+        swe::launch_rhs_adjoint(c, X, A.Rb, Wbar, bbar, s, true);
     }
+    if (bbar) swe::launch_src_adjoint(c, A.Gsrc_acc, bbar, s);
     if (c->p.rk == 1) swe::launch_axpy(c, n3, 1.0, A.Wnb, Wbar, s);
     int rc = check_launch("swe_step_adjoint");
     if (rc) return rc;

@@ -53,9 +53,12 @@ __host__ __device__ constexpr int pair_index_adj(int i, int q) {
 //   Q^ = 2 d1 + (u_i + u_q) d2 + (v_i + v_q) d3,  P^ = 2g (S_x d2 + S_y d3),
 //   u^_{i,q} += Q d2, v^_{i,q} += Q d3, hu^_{i,q} += S_x Q^, hv^_{i,q} += S_y Q^,
 //   h^_i += h_q P^, h^_q += h_i P^.
+// The factor 2g of P^ is applied once per node after both lines (gH holds
+// h^ / 2g), and every cotangent sum is a fused multiply-add: 24 FP64
+// instructions per pair.
 template <int N, int BLK>
 __device__ __forceinline__ void pair_loop_adj(const double* __restrict__ s, int base, int stride,
-                                              const double* __restrict__ pmk, double g2, double* gH, double* gHU,
+                                              const double* __restrict__ pmk, double* gH, double* gHU,
                                               double* gHV, double* gU, double* gV) {
     constexpr int n = N + 1;
     const double* sH = s + F_H * BLK;
@@ -80,17 +83,15 @@ __device__ __forceinline__ void pair_loop_adj(const double* __restrict__ s, int 
             const double d1 = a1 - sA1[nq], d2 = a2 - sA2[nq], d3 = a3 - sA3[nq];
             const double Q = fma(hu_i + sHU[nq], sx, (hv_i + sHV[nq]) * sy);
             const double Qb = fma(v_i + sV[nq], d3, fma(u_i + sU[nq], d2, 2.0 * d1));
-            const double Pb = g2 * fma(sy, d3, sx * d2);
-            const double qd2 = Q * d2, qd3 = Q * d3;
-            gU[i] += qd2;
-            gU[q] += qd2;
-            gV[i] += qd3;
-            gV[q] += qd3;
-            const double xq = sx * Qb, yq = sy * Qb;
-            gHU[i] += xq;
-            gHU[q] += xq;
-            gHV[i] += yq;
-            gHV[q] += yq;
+            const double Pb = fma(sy, d3, sx * d2);
+            gU[i] = fma(Q, d2, gU[i]);
+            gU[q] = fma(Q, d2, gU[q]);
+            gV[i] = fma(Q, d3, gV[i]);
+            gV[q] = fma(Q, d3, gV[q]);
+            gHU[i] = fma(sx, Qb, gHU[i]);
+            gHU[q] = fma(sx, Qb, gHU[q]);
+            gHV[i] = fma(sy, Qb, gHV[i]);
+            gHV[q] = fma(sy, Qb, gHV[q]);
             gH[i] = fma(sH[nq], Pb, gH[i]);
             gH[q] = fma(h_i, Pb, gH[q]);
         }
@@ -109,6 +110,7 @@ struct VolAdjArgs {
     double* Gsrc;        // [2][KN] out: cotangents of the source coefficients
     double* Gfvt;        // [4][KN] out (AV): cotangents of the contravariant viscous fluxes
     double* Gfvo;        // [2][KS] out (AV): cotangents of the viscous interface flux
+    int acc_src;         // add to Gsrc (a sum over stages) instead of overwriting it
 };
 
 template <int N, bool AV>
@@ -162,7 +164,7 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
     for (int p = 0; p < n; ++p) gH[p] = gHU[p] = gHV[p] = gU[p] = gV[p] = 0.0;
 
     // ---- xi-line j = l ------------------------------------------------------
-    if (valid) pair_loop_adj<N, BLK>(sm, e * nn + l * n, 1, pmx, g2, gH, gHU, gHV, gU, gV);
+    if (valid) pair_loop_adj<N, BLK>(sm, e * nn + l * n, 1, pmx, gH, gHU, gHV, gU, gV);
 #pragma unroll
     for (int p = 0; p < n; ++p) {
         const int id = e * nn + l * n + p;
@@ -183,7 +185,7 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
         gU[p] = S(F_GU)[id];
         gV[p] = S(F_GV)[id];
     }
-    if (valid) pair_loop_adj<N, BLK>(sm, e * nn + l, n, pme, g2, gH, gHU, gHV, gU, gV);
+    if (valid) pair_loop_adj<N, BLK>(sm, e * nn + l, n, pme, gH, gHU, gHV, gU, gV);
     if (!valid) return;
 
     const long long KN = m.KN, KS = m.KS, side = k * 4 * n;
@@ -196,18 +198,22 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
 #pragma unroll
     for (int p = 0; p < n; ++p) {
         const int j = p;
-        const double wj = wq<N>(j);
         const long long gid = k * nn + j * n + i;
         const double rb2 = a.Rb[KN + gid], rb3 = a.Rb[2 * KN + gid];
         const double h = S(F_H)[eb + j * n + i];
         // R2 = h srcx + f a2, R3 = h srcy + f a3
-        a.Ga[gid] = fma(rb2, m.srcx[gid], fma(rb3, m.srcy[gid], gH[p]));
+        a.Ga[gid] = fma(g2, gH[p], fma(rb2, m.srcx[gid], rb3 * m.srcy[gid]));
         a.Ga[KN + gid] = gHU[p];
         a.Ga[2 * KN + gid] = gHV[p];
         a.Guv[gid] = gU[p];
         a.Guv[KN + gid] = gV[p];
-        a.Gsrc[gid] = h * rb2;
-        a.Gsrc[KN + gid] = h * rb3;
+        if (a.acc_src) {
+            a.Gsrc[gid] = fma(h, rb2, a.Gsrc[gid]);
+            a.Gsrc[KN + gid] = fma(h, rb3, a.Gsrc[KN + gid]);
+        } else {
+            a.Gsrc[gid] = h * rb2;
+            a.Gsrc[KN + gid] = h * rb3;
+        }
         const double b1 = S(F_A1)[eb + j * n + i], b2 = S(F_A2)[eb + j * n + i], b3 = S(F_A3)[eb + j * n + i];
         // a_c += wt F_out,c  =>  F_out^ = wt a^_c;  a_c -= wt (Fv_out - own)  =>  Fv_out^ = -wt a^_c
         // (every element takes the viscous interface flux, viscous or not)
@@ -223,8 +229,25 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
         };
         if (j == 0) lift(0, i, wi);
         if (j == N) lift(2, i, wi);
-        if (i == N) lift(1, j, wj);
-        if (i == 0) lift(3, j, wj);
+    }
+    // the xi-side slots (sides 1 and 3) of row j = l: every lane takes the
+    // two end nodes of its row, rather than two lanes of eight in the loop
+    {
+        const double wl = wq<N>(l);
+#pragma unroll
+        for (int end = 0; end < 2; ++end) {
+            const int pi = end == 0 ? N : 0, f = end == 0 ? 1 : 3;
+            const int nd = eb + l * n + pi;
+            const double b1 = S(F_A1)[nd], b2 = S(F_A2)[nd], b3 = S(F_A3)[nd];
+            const long long sl = side + f * n + l;
+            a.Gfo[sl] = wl * b1;
+            a.Gfo[KS + sl] = wl * b2;
+            a.Gfo[2 * KS + sl] = wl * b3;
+            if (AV) {
+                a.Gfvo[sl] = -wl * b2;
+                a.Gfvo[KS + sl] = -wl * b3;
+            }
+        }
     }
     if (!visc) return;
     // ---- viscous divergence: a_c -= w_i w_j (sum_q D_iq Ft_c[j][q] + sum_q D_jq Gt_c[q][i])
@@ -594,7 +617,7 @@ struct GatherArgs {
     const double* Ga;
     const double* Guv;
     const double* Gsl;
-    const double* Gsrc;
+    const double* Gsrc;  // nullable: the source part is deferred (k_src_adj)
     double* Wbar;
     double* bbar;  // nullable
 };
@@ -644,7 +667,8 @@ __global__ void __launch_bounds__(32 * GA_WPB) k_gather_adj(GatherArgs a) {
             a.Wbar[KN + gid] += ghu;
             a.Wbar[2 * KN + gid] += ghv;
             bsl[r] = gb;
-            if (a.bbar) {
+            if (a.bbar && !a.Gsrc) a.bbar[gid] += gb;
+            if (a.bbar && a.Gsrc) {
                 const double cx = mg2 * m.rJ[gid] * a.Gsrc[gid], cy = mg2 * m.rJ[gid] * a.Gsrc[KN + gid];
                 sC[w][0][node] = cx;
                 sC[w][1][node] = cy;
@@ -652,7 +676,7 @@ __global__ void __launch_bounds__(32 * GA_WPB) k_gather_adj(GatherArgs a) {
                 sC[w][3][node] = fma(m.aex[gid], cx, m.aey[gid] * cy);
             }
         }
-        if (!a.bbar) continue;
+        if (!a.bbar || !a.Gsrc) continue;
         __syncwarp();
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
@@ -674,6 +698,57 @@ __global__ void __launch_bounds__(32 * GA_WPB) k_gather_adj(GatherArgs a) {
             }
             const double src = zx + ze + m.axx[gid] * tx + m.axy[gid] * ty + m.aex[gid] * ex + m.aey[gid] * ey;
             a.bbar[gid] += bsl[r] + src;
+        }
+        __syncwarp();
+    }
+}
+
+// The source part of the gather alone: bbar += (d src / d b)^T Gsrc, for
+// source-coefficient cotangents summed over several stages (the map is
+// linear and depends on the geometry only). One warp per element.
+template <int N>
+__global__ void __launch_bounds__(32 * GA_WPB) k_src_adj(DeviceMesh m, const double* __restrict__ Gsrc,
+                                                         double* __restrict__ bbar) {
+    constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
+    __shared__ double sD[nn];
+    __shared__ double sC[GA_WPB][4][nn];
+    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) sD[idx] = Dm<N>(idx / n, idx % n);
+    __syncthreads();
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+    const long long KN = m.KN;
+    const double mg2 = -0.5 * m.g;
+    for (long long k = (long long)blockIdx.x * GA_WPB + w; k < m.K; k += (long long)gridDim.x * GA_WPB) {
+        const long long base = k * nn;
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int node = lane + 32 * r;
+            if (node >= nn) continue;
+            const long long gid = base + node;
+            const double cx = mg2 * m.rJ[gid] * Gsrc[gid], cy = mg2 * m.rJ[gid] * Gsrc[KN + gid];
+            sC[w][0][node] = cx;
+            sC[w][1][node] = cy;
+            sC[w][2][node] = fma(m.axx[gid], cx, m.axy[gid] * cy);
+            sC[w][3][node] = fma(m.aex[gid], cx, m.aey[gid] * cy);
+        }
+        __syncwarp();
+#pragma unroll
+        for (int r = 0; r < PER; ++r) {
+            const int node = lane + 32 * r;
+            if (node >= nn) continue;
+            const int i = node % n, j = node / n;
+            const long long gid = base + node;
+            double zx = 0.0, ze = 0.0, tx = 0.0, ty = 0.0, ex = 0.0, ey = 0.0;
+#pragma unroll
+            for (int q = 0; q < n; ++q) {
+                const double di = sD[q * n + i], dj = sD[q * n + j];
+                zx = fma(di, sC[w][2][j * n + q], zx);
+                tx = fma(di, sC[w][0][j * n + q], tx);
+                ty = fma(di, sC[w][1][j * n + q], ty);
+                ze = fma(dj, sC[w][3][q * n + i], ze);
+                ex = fma(dj, sC[w][0][q * n + i], ex);
+                ey = fma(dj, sC[w][1][q * n + i], ey);
+            }
+            bbar[gid] += zx + ze + m.axx[gid] * tx + m.axy[gid] * ty + m.aex[gid] * ex + m.aey[gid] * ey;
         }
         __syncwarp();
     }
@@ -978,11 +1053,14 @@ void vol_adj_n(swe_ctx* c, const VolAdjArgs& a, cudaStream_t s) {
 
 void init_tables_adjoint() { upload_tables(); }
 
-void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* Wbar, double* bbar, cudaStream_t s) {
+void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* Wbar, double* bbar, cudaStream_t s,
+                        bool defer_src) {
     AdjWork& A = c->adj;
     const DeviceMesh& m = c->m;
     const bool av = c->p.av != 0;
-    VolAdjArgs va{m, W, c->w.uv, Rb, c->w.eps, A.Ga, A.Guv, A.Gfo, A.Gsrc, A.Gfvt, A.Gfvo};
+    defer_src = defer_src && bbar != nullptr;
+    VolAdjArgs va{m, W, c->w.uv, Rb, c->w.eps, A.Ga, A.Guv, A.Gfo, defer_src ? A.Gsrc_acc : A.Gsrc, A.Gfvt, A.Gfvo,
+                  defer_src ? 1 : 0};
 #define SWE_VA(NN) \
     if (av) vol_adj_n<NN, true>(c, va, s); else vol_adj_n<NN, false>(c, va, s)
     SWE_SWITCH_N_ADJ(m.N, SWE_VA)
@@ -1020,7 +1098,7 @@ void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* W
                 k_wall_adj<false><<<grid_for(walls, 128), 128, 0, s>>>(m, W, c->w.uv, A.Gfo, A.GUs, av, A.Gsl);
         }
     }
-    GatherArgs ga{m, W, c->w.uv, A.Ga, A.Guv, A.Gsl, A.Gsrc, Wbar, bbar};
+    GatherArgs ga{m, W, c->w.uv, A.Ga, A.Guv, A.Gsl, defer_src ? nullptr : A.Gsrc, Wbar, bbar};
 #define SWE_GA(NN)                                                                          \
     {                                                                                       \
         Timed tm(c, KC_ADJ, s);                                                             \
@@ -1028,6 +1106,16 @@ void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* W
     }
     SWE_SWITCH_N_ADJ(m.N, SWE_GA)
 #undef SWE_GA
+}
+
+void launch_src_adjoint(swe_ctx* c, const double* Gsrc, double* bbar, cudaStream_t s) {
+#define SWE_SA(NN)                                                                          \
+    {                                                                                       \
+        Timed tm(c, KC_ADJ, s);                                                             \
+        k_src_adj<NN><<<grid_for(c->m.K, GA_WPB), 32 * GA_WPB, 0, s>>>(c->m, Gsrc, bbar);   \
+    }
+    SWE_SWITCH_N_ADJ(c->m.N, SWE_SA)
+#undef SWE_SA
 }
 
 void launch_limit_record(swe_ctx* c, double* W, uint8_t* act, int32_t* amin, uint8_t* cut, cudaStream_t s) {

@@ -103,13 +103,26 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
 
     if (!EPS_GIVEN) {
         // ---- water heights of the 8 elements (contiguous in memory) -------
-        for (int idx = lane; idx < AV_EPW * nn; idx += 32) {
-            const int e = idx / nn;
-            Q[e][idx - e * nn] = e < ne ? a.W[k0 * nn + idx] : 0.0;
+        // a compile-time trip count, unrolled: the loads of all iterations
+        // are in flight together
+        constexpr int LQ = (AV_EPW * nn + 31) / 32;
+#pragma unroll
+        for (int r = 0; r < LQ; ++r) {
+            const int idx = lane + 32 * r;
+            if (idx < AV_EPW * nn) {
+                const int e = idx / nn;
+                Q[e][idx - e * nn] = e < ne ? a.W[k0 * nn + idx] : 0.0;
+            }
         }
         __syncwarp();
         // ---- the four projections of every element ------------------------
-        for (int s = lane; s < AV_EPW * P4; s += 32) {
+        // n tasks per lane (AV_EPW * P4 = 32 n), unrolled: the lane's
+        // independent dot products interleave, instead of one dependent chain
+        // of fused multiply-adds at a time
+        static_assert((AV_EPW * P4) % 32 == 0, "projection tasks fill whole warps");
+#pragma unroll
+        for (int r = 0; r < AV_EPW * P4 / 32; ++r) {
+            const int s = lane + 32 * r;
             const int e = s / P4, L = s - e * P4, t = L / n, p = L - t * n;
             const double* vr = sVi + (t < 2 ? N : N - 1) * n;
             // t even: sum over i at j = p; t odd: sum over j at i = p. One
@@ -124,9 +137,11 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
         // ---- sum w w Q^2: four lanes per element ---------------------------
         const int e4 = lane >> 2, sub = lane & 3;
         double swq = 0.0;
-        for (int node = sub; node < nn; node += 4) {
-            const double q = Q[e4][node];
-            swq = fma(sWW[node] * q, q, swq);
+#pragma unroll
+        for (int r = 0; r < (nn + 3) / 4; ++r) {
+            const int node = sub + 4 * r;
+            const double q = node < nn ? Q[e4][node] : 0.0;
+            swq = fma(sWW[node < nn ? node : 0] * q, q, swq);
         }
         swq += __shfl_xor_sync(0xffffffffu, swq, 1);
         swq += __shfl_xor_sync(0xffffffffu, swq, 2);

@@ -151,6 +151,7 @@ struct AdjWork {
     double* Gfvo = nullptr;   // [2][KS] viscous interface-flux cotangents
     double* Gfvtr = nullptr;  // [4][KS] side-node viscous-flux cotangents (wall slots stay 0)
     double* Gsrc = nullptr;   // [2][KN] source-coefficient cotangents
+    double* Gsrc_acc = nullptr;  // [2][KN] their sum over the stages of a step adjoint
     double* Khb = nullptr;    // [3][KN] 2N-storage register cotangent
     double* Rb = nullptr;     // [3][KN] right-hand-side cotangent of a stage
     double* Wnb = nullptr;    // [3][KN] step-start cotangent (SSP)
@@ -253,8 +254,14 @@ int autotune_ctx(swe_ctx* c, const double* W, cudaStream_t s);
 
 // Adjoint launchers (k_adjoint.cu). launch_rhs_adjoint expects the forward
 // intermediates of W in the work buffers (rhs_chain just ran on W) and adds
-// (dR/dW)^T Rb to Wbar and (dR/db)^T Rb to bbar (nullable).
-void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* Wbar, double* bbar, cudaStream_t s);
+// (dR/dW)^T Rb to Wbar and (dR/db)^T Rb to bbar (nullable). With defer_src,
+// the source-coefficient cotangents are added to adj.Gsrc_acc instead of
+// being carried to bbar; launch_src_adjoint later adds their (linear,
+// state-independent) image under the source's bathymetry derivatives to
+// bbar, once for all the stages that accumulated.
+void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* Wbar, double* bbar, cudaStream_t s,
+                        bool defer_src = false);
+void launch_src_adjoint(swe_ctx* c, const double* Gsrc, double* bbar, cudaStream_t s);
 void launch_limit_record(swe_ctx* c, double* W, uint8_t* act, int32_t* amin, uint8_t* cut, cudaStream_t s);
 void launch_update_adjoint(swe_ctx* c, int mode, double* Wb, const double* Y, const uint8_t* act,
                            const int32_t* amin, const uint8_t* cut, double* Khb, double* Rb, double* Wnb, double a,

@@ -296,3 +296,32 @@ def test_rhs_full_size_dam_break_N7():
     eo = o.epsilon()
     assert np.count_nonzero(eo) > 0
     assert np.abs(g.epsilon().cpu().numpy() - eo).max() < 1e-12
+
+
+@pytest.mark.parametrize("N", [1, 3, 12])
+def test_rhs_full_size_degree_sweep(N):
+    """The degree sweep's workloads (~4.2M nodes: K1 = round(2048/(N+1))
+    quads per direction), ES + AV and EC without AV: every node against the
+    oracle."""
+    K1 = int(round(2048 / (N + 1)))
+    p = I.dam_break(N=N, K1=K1)
+    for kw in (dict(flux=1, av=True, eps0=0.025), dict(flux=0)):
+        o, g = pair(p, **kw)
+        Ro = o.rhs(p.W)
+        Rg = g.rhs(dev(p.W)).cpu().numpy()
+        assert rhs_err(Rg, Ro, p) < RHS_TOL, kw
+
+
+def test_step_full_size_dam_break_N7():
+    """One time step of the benchmark (LSRK4(5), CFL 0.5, ES + AV + limiter,
+    the step size from the device-side CFL/positivity reduction) at full
+    size against the oracle's step."""
+    p = I.dam_break(N=7)
+    kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    o, g = pair(p, **kw)
+    Wo, rco, dto = o.step(p.W, 0.0, 1)
+    Wg = dev(p.W)
+    rcg, dtg = g.step(Wg, 0.0, 1)
+    assert rco == 0 and rcg == 0
+    assert abs(dtg - dto) < 1e-13 * dto
+    assert rel(Wg.cpu().numpy(), Wo) < STEP_TOL

@@ -14,7 +14,8 @@ steps:
     scheme), element means non-negative;
   * accuracy: the L1 error of h against the analytic solution at the final
     time is small and decreases under mesh refinement (32^2, 64^2, 128^2
-    quads at one final time), the trend the paper reports for this case.
+    quads at one final time), the trend the paper reports for this case; the
+    GPU's errors agree with the oracle's (8.320e-4 and 8.318e-4 at 128^2).
 """
 import math
 
@@ -114,8 +115,8 @@ def test_thacker_error_decreases_under_refinement():
         t, n = run_to(g, Wg, T, 20000)
         assert abs(t - T) < 1e-12
         errs.append(l1_error(p, Wg.cpu().numpy(), t, quad_weights(p)))
-    # The oracle gives 3.35e-3 (32^2) and 1.28e-3 (64^2) on this case: about
-    # first order, as expected with a dry front. Check the decrease with
-    # margin and the size at 128^2.
-    assert errs[0] > 1.6 * errs[1] > 1.6 * 1.6 * errs[2], errs
-    assert errs[2] < 1e-3, errs
+    # The oracle gives 3.35e-3 (32^2), 1.28e-3 (64^2) and 8.32e-4 (128^2) on
+    # this case: the rate falls below first order as the dry front dominates
+    # the error. Check the decrease with margin and the size at 128^2.
+    assert errs[0] > 1.3 * errs[1] > 1.3 * 1.3 * errs[2], errs
+    assert errs[2] < 9e-4, errs
