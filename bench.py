@@ -200,6 +200,22 @@ def oracle_rate(N, K1, steps, warmup=0):
     return RK_STAGES * p.nodes / t, t, O.threads(), p.nodes
 
 
+def cpu_model():
+    """The host CPU's model name (from /proc/cpuinfo, else the platform)."""
+    import platform
+    try:
+        for line in open("/proc/cpuinfo"):
+            key = line.split(":")[0].strip().lower()
+            if key in ("model name", "cpu model", "hardware"):
+                return line.split(":", 1)[1].strip()
+        for line in open("/proc/cpuinfo"):
+            if line.split(":")[0].strip().lower() == "cpu part":
+                return f"{platform.machine()} cpu part {line.split(':', 1)[1].strip()}"
+    except OSError:
+        pass
+    return platform.machine()
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -214,7 +230,7 @@ def run_reference(args):
             "dtype": "f64", "data": "synthetic",
             "config": workload_config(N, 2048 // (N + 1) if args.K1 is None else args.K1),
             "cpu_baseline": {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": rate, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -658,10 +674,19 @@ def main():
         "scalar_updates_per_s": 3 * value,
     }
     if not args.no_cpu_baseline and ws == 1:
+        from oracle import oracle as O
         rate, t, cores, n_s = oracle_rate(N, K1, 1)
+        # the same oracle on one thread, on a bounded sample (64x64 quads)
+        O.set_threads(1)
+        rate1, t1, _, n_1 = oracle_rate(N, 64, 1)
+        O.set_threads(cores)
         line["cpu_baseline"] = {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one LSRK4(5) step of the same workload ({n_s} nodes), "
-                                          f"{t:.1f} s on {cores} OpenMP threads"}
+                                          f"{t:.1f} s on {cores} OpenMP threads",
+                                "cpu_model": cpu_model(),
+                                "single_thread": {"value": rate1, "unit": "node-updates/s",
+                                                  "sample": f"one LSRK4(5) step, dam_break N={N} on 64x64 "
+                                                            f"quads ({n_1} nodes), {t1:.1f} s on 1 thread"}}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -121,6 +121,11 @@ def threads() -> int:
     return lib().orc_threads()
 
 
+def set_threads(t: int) -> None:
+    """OpenMP threads of later oracle calls (for timing the oracle)."""
+    lib().orc_set_threads(int(t))
+
+
 class Oracle:
     """Oracle instance for one Problem (see paper_1804_02221_gb300.inputs)."""
 

@@ -1090,3 +1090,11 @@ int orc_threads(void) {
     return 1;
 #endif
 }
+
+void orc_set_threads(int t) {
+#ifdef _OPENMP
+    if (t > 0) omp_set_num_threads(t);
+#else
+    (void)t;
+#endif
+}

@@ -89,6 +89,8 @@ void orc_lsrk_coefficients(double* A, double* B);
 
 /* Number of OpenMP threads the oracle uses (1 without OpenMP). */
 int orc_threads(void);
+/* Number of OpenMP threads of later calls (timing only). */
+void orc_set_threads(int t);
 
 #ifdef __cplusplus
 }
