@@ -178,20 +178,14 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
     }
     __syncwarp();
 
-    // ---- viscous fluxes of the viscous elements, zeros elsewhere -----------
+    // ---- viscous fluxes of the viscous elements ------------------------------
     const long long KS = m.KS, KN = m.KN;
     for (int e = 0; e < ne; ++e) {
         const double ep = sEps[w][e];
         const long long k = k0 + e, base = k * nn, side = k * 4 * n;
-        if (!(ep > 0.0)) {
-            for (int s = lane; s < 4 * n; s += 32) {
-                a.Fvtr[side + s] = 0.0;
-                a.Fvtr[KS + side + s] = 0.0;
-                a.Fvtr[2 * KS + side + s] = 0.0;
-                a.Fvtr[3 * KS + side + s] = 0.0;
-            }
-            continue;
-        }
+        // inviscid elements leave their side-node viscous fluxes unwritten:
+        // the interface average reads only the traces of viscous elements
+        if (!(ep > 0.0)) continue;
         double* H = Q[e];
         double* U = sUV[w][0];
         double* V = sUV[w][1];

@@ -127,19 +127,30 @@ __global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double*
 
 // ---------------------------------------------------------------------------
 // BR1 viscous interface flux {F^v . n} (Thm. 1) with the owner's unscaled
-// outward normal; +avg to the owner's slot, -avg to the neighbour's.
+// outward normal; +avg to the owner's slot, -avg to the neighbour's. Only
+// viscous elements (eps_k > 0) carry side-node viscous fluxes: the other
+// side's traces count as zero and are not read, and a face between two
+// inviscid elements gets zero without reading any.
 // ---------------------------------------------------------------------------
-__global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, double* __restrict__ Fvout,
-                            const int* stop) {
+__global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, const double* __restrict__ eps,
+                            double* __restrict__ Fvout, const int* stop) {
     if (stopped(stop)) return;
     const long long total = (long long)m.nfaces * m.n;
+    const long long S = m.KS, sps = 4LL * m.n;  // side slots per element
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long tm = m.f_tm[t], tp = m.f_tp[t];
-        const double nx = m.f_sx[t], ny = m.f_sy[t];
-        const long long S = m.KS;
-        const double a2 = 0.5 * fma(nx, Fvtr[tm] + Fvtr[tp], ny * (Fvtr[2 * S + tm] + Fvtr[2 * S + tp]));
-        const double a3 = 0.5 * fma(nx, Fvtr[S + tm] + Fvtr[S + tp], ny * (Fvtr[3 * S + tm] + Fvtr[3 * S + tp]));
+        const bool vm = nonzero(eps[tm / sps]), vp = nonzero(eps[tp / sps]);
+        double a2 = 0.0, a3 = 0.0;
+        if (vm || vp) {
+            const double F2 = (vm ? Fvtr[tm] : 0.0) + (vp ? Fvtr[tp] : 0.0);
+            const double F3 = (vm ? Fvtr[S + tm] : 0.0) + (vp ? Fvtr[S + tp] : 0.0);
+            const double G2 = (vm ? Fvtr[2 * S + tm] : 0.0) + (vp ? Fvtr[2 * S + tp] : 0.0);
+            const double G3 = (vm ? Fvtr[3 * S + tm] : 0.0) + (vp ? Fvtr[3 * S + tp] : 0.0);
+            const double nx = m.f_sx[t], ny = m.f_sy[t];
+            a2 = 0.5 * fma(nx, F2, ny * G2);
+            a3 = 0.5 * fma(nx, F3, ny * G3);
+        }
         Fvout[tm] = a2;
         Fvout[S + tm] = a3;
         Fvout[tp] = negated(a2);
@@ -556,7 +567,7 @@ void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop) {
     const long long total = (long long)c->m.nfaces * c->m.n;
     if (total == 0) return;
     Timed tm(c, KC_VFACE, s);
-    k_visc_face<<<grid_for(total, 128), 128, 0, s>>>(c->m, c->w.Fvtr, c->w.Fvout, stop);
+    k_visc_face<<<grid_for(total, 128), 128, 0, s>>>(c->m, c->w.Fvtr, c->w.eps, c->w.Fvout, stop);
 }
 
 void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,

@@ -88,12 +88,6 @@ constexpr int vol_min_blocks() {
     return b > 0 ? b : 1;
 }
 
-// x != 0 (either sign of zero counts as zero), from the bit pattern: an
-// integer test, so that it costs no FP64 instruction.
-__device__ __forceinline__ bool nonzero(double x) {
-    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ULL;
-}
-
 template <int N>
 __host__ __device__ constexpr int pair_index(int i, int q) {
     return i * (N + 1) - i * (i + 1) / 2 + (q - i - 1);

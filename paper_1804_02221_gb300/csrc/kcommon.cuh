@@ -76,6 +76,12 @@ __device__ __forceinline__ double sqrt_pos(double x) {
     return fma(hy, fma(-s, s, x), s);
 }
 
+// x != 0 (either sign of zero counts as zero), from the bit pattern: an
+// integer test, so that it costs no FP64 instruction.
+__device__ __forceinline__ bool nonzero(double x) {
+    return ((unsigned long long)__double_as_longlong(x) << 1) != 0ULL;
+}
+
 // max(x, 0) by the sign bit (an integer test, no FP64 instruction).
 __device__ __forceinline__ double pos_part(double x) {
     return (long long)__double_as_longlong(x) > 0 ? x : 0.0;

@@ -127,6 +127,7 @@ struct Work {
     double* Ustar;  // [2][KS] BR1 interface values
     double* Fvt;    // [4][KN] contravariant viscous fluxes Ft2, Ft3, Gt2, Gt3
     double* Fvtr;   // [4][KS] physical viscous fluxes at side nodes F2, F3, G2, G3
+                    // (written for viscous elements only; read only for them)
     double* Fvout;  // [2][KS] outward viscous interface flux
     double* eps;    // [K]
     double* Kreg;   // [3][KN] 2N-storage register
