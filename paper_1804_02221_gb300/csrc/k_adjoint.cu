@@ -461,7 +461,12 @@ __global__ void __launch_bounds__(32 * AVA_WPB) k_av_adj(AvAdjArgs a) {
 // Interface flux in reverse. normal_flux_adj differentiates the flux of the
 // forward kernel in the normal frame (same expression, same branches).
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double sgn(double x) { return x > 0.0 ? 1.0 : (x < 0.0 ? -1.0 : 0.0); }
+// sgn(x) y (zero for x = 0) by the sign bits: integer operations only.
+__device__ __forceinline__ double sgn_times(double x, double y) {
+    const unsigned long long bx = (unsigned long long)__double_as_longlong(x);
+    if ((bx << 1) == 0ULL) return 0.0;
+    return __longlong_as_double(__double_as_longlong(y) ^ (long long)(bx & 0x8000000000000000ULL));
+}
 
 template <bool ES>
 __device__ __forceinline__ void normal_flux_adj(double g, double r2g, double hm, double hp, double utm, double utp,
@@ -472,7 +477,7 @@ __device__ __forceinline__ void normal_flux_adj(double g, double r2g, double hm,
     double hab = 0.0, uab = 0.0, vab = 0.0, h2ab = 0.0;
     hmb = hpb = utmb = utpb = vtmb = vtpb = bmb = bpb = 0.0;
     if (ES) {
-        const double cm = hm > 0.0 ? sqrt(g * hm) : 0.0, cp = hp > 0.0 ? sqrt(g * hp) : 0.0;
+        const double cm = sqrt_pos(g * pos_part(hm)), cp = sqrt_pos(g * pos_part(hp));
         const double ca = 0.5 * (cm + cp);
         const double gH = g * ((hp + bp) - (hm + bm));
         const double dut = utp - utm, dvt = vtp - vtm;
@@ -489,13 +494,13 @@ __device__ __forceinline__ void normal_flux_adj(double g, double r2g, double hm,
         const double lam2b = -0.5 * dvt * F3b;
         const double dvtb = -0.5 * lam2 * F3b;
         const double A1b = s1b * B1, B1b = s1b * A1, A3b = s3b * B3, B3b = s3b * A3;
-        const double sp = sgn(ua + ca) * r2g * A1b, sm = sgn(ua - ca) * r2g * A3b;
+        const double sp = sgn_times(ua + ca, r2g * A1b), sm = sgn_times(ua - ca, r2g * A3b);
         uab += sp + sm;
         cab += sp - sm;
         cab += (B1b - B3b) * dut;
         const double dutb = ca * (B1b - B3b);
         const double gHb = g * (B1b + B3b);
-        const double sl = sgn(ha * ua) * lam2b;
+        const double sl = sgn_times(ha * ua, lam2b);
         hab += sl * ua;
         uab += sl * ha;
         hpb += gHb;
@@ -507,8 +512,9 @@ __device__ __forceinline__ void normal_flux_adj(double g, double r2g, double hm,
         vtpb += dvtb;
         vtmb -= dvtb;
         // c = sqrt(g h): dc/dh = g/(2c) for h > 0
-        if (hm > 0.0) hmb += 0.5 * cab * g / (2.0 * cm);
-        if (hp > 0.0) hpb += 0.5 * cab * g / (2.0 * cp);
+        const double qg = 0.25 * g * cab;
+        if (hm > 0.0) hmb += qg * recip_pos(cm);
+        if (hp > 0.0) hpb += qg * recip_pos(cp);
     }
     // EC part: F1 = ha ua, F2 = F1 ua + g h2a / 2, F3 = F1 va
     const double F1 = ha * ua;
