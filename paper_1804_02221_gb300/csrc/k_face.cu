@@ -352,56 +352,80 @@ struct DtArgs {
     const int* stop;
 };
 
+// Non-negative doubles order like their bit patterns: max by an integer
+// comparison (no FP64 instruction).
+__device__ __forceinline__ unsigned long long max_bits(unsigned long long a, double x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+    return b > a ? b : a;
+}
+
+constexpr int DT_WPB = 4;  // warps (elements) per block of the time-step kernel
+
+// One element on one warp. The celerities c = sqrt(g max(h, 0)) of the CFL
+// part are kept in shared memory (sc, the warp's n*n slots) for the own side
+// of the positivity part. The maxima of non-negative values and the sign
+// tests are integer operations on the bit patterns.
 template <int N>
-__device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lane) {
+__device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lane, double* sc) {
     constexpr int n = N + 1, nn = n * n;
     const DeviceMesh& m = a.m;
     const double g = m.g;
-    double lam = 0.0;
+    unsigned long long lamb = 0;
     for (int node = lane; node < nn; node += 32) {
         const long long id = k * nn + node;
         const double h = a.W[id], u = a.uv[id], v = a.uv[m.KN + id];
         const double c = sqrt_pos(g * pos_part(h));
+        sc[node] = c;
         const double vel = fabs(fma(m.axx[id], u, m.axy[id] * v)) + fabs(fma(m.aex[id], u, m.aey[id] * v));
-        lam = fmax(lam, fma(c, a.cfl_n[id], m.rJ[id] * vel));
+        lamb = max_bits(lamb, fma(c, a.cfl_n[id], m.rJ[id] * vel));
     }
-    lam = warp_max(lam);
+    const double lam = warp_max(__longlong_as_double((long long)lamb));
     unsigned long long* bits = a.bits + 2 * (m.inst ? m.inst[k] : 0);
     if (lane == 0 && lam > 0.0) atomic_max_pos(&bits[0], lam);
-    if (!a.pos) return;  // uniform: the flag is a kernel argument
-    double inv = 0.0;
-    for (int sn = lane; sn < 4 * n; sn += 32) {
-        const int f = sn / n, p = sn - f * n;
-        const int i = (f == 0 || f == 2) ? p : (f == 1 ? N : 0);
-        const int j = (f == 1 || f == 3) ? p : (f == 2 ? N : 0);
-        const long long own = k * nn + j * n + i;
-        const long long slot = k * 4 * n + sn;
-        const long long sb = m.s_nb[slot];
-        const bool wall = sb < 0;  // solid wall: the mirror state
-        const long long nb = wall ? own : sb;
-        const double nx = m.s_nx[slot], ny = m.s_ny[slot], rwa = m.s_rwa[slot];
-        const double hm = a.W[own], hp = a.W[nb];
-        const double utm = fma(nx, a.uv[own], ny * a.uv[m.KN + own]);
-        const double utp = wall ? -utm : fma(nx, a.uv[nb], ny * a.uv[m.KN + nb]);
-        const double ua = 0.5 * (utm + utp);
-        const double ca = sqrt_pos(m.g4 * pos_part(hm)) + sqrt_pos(m.g4 * pos_part(hp));
-        const double ap = fabs(ua + ca), am = fabs(ua - ca);
-        const double A = ap + am, B = ap - am;
-        const double i1 = fma(2.0, ua, A) * rwa;
-        if (i1 > 0.0) inv = fmax(inv, i1);
-        const double jump = utp - utm;
-        if (hm > 0.0 && B * jump < 0.0) inv = fmax(inv, fabs(ca * B * jump) * rwa * recip_pos(g * hm));
+    if (a.pos) {  // uniform: the flag is a kernel argument
+        __syncwarp();
+        unsigned long long invb = 0;
+        for (int sn = lane; sn < 4 * n; sn += 32) {
+            const int f = sn / n, p = sn - f * n;
+            const int i = (f == 0 || f == 2) ? p : (f == 1 ? N : 0);
+            const int j = (f == 1 || f == 3) ? p : (f == 2 ? N : 0);
+            const int ownl = j * n + i;
+            const long long own = k * nn + ownl;
+            const long long slot = k * 4 * n + sn;
+            const long long sb = m.s_nb[slot];
+            const bool wall = sb < 0;  // solid wall: the mirror state
+            const long long nb = wall ? own : sb;
+            const double nx = m.s_nx[slot], ny = m.s_ny[slot], rwa = m.s_rwa[slot];
+            const double hm = a.W[own], hp = a.W[nb];
+            const double utm = fma(nx, a.uv[own], ny * a.uv[m.KN + own]);
+            const double utp = wall ? -utm : fma(nx, a.uv[nb], ny * a.uv[m.KN + nb]);
+            const double ua = 0.5 * (utm + utp);
+            const double cm = sc[ownl], cp = wall ? cm : sqrt_pos(g * pos_part(hp));
+            const double ca = 0.5 * (cm + cp);
+            const double ap = fabs(ua + ca), am = fabs(ua - ca);
+            const double A = ap + am, B = ap - am;
+            const double i1 = fma(2.0, ua, A) * rwa;
+            if ((long long)__double_as_longlong(i1) > 0) invb = max_bits(invb, i1);
+            const double jump = utp - utm;
+            // h- > 0 and B [[u~]] < 0 (nonzero factors of opposite signs)
+            const unsigned long long bB = (unsigned long long)__double_as_longlong(B),
+                                     bJ = (unsigned long long)__double_as_longlong(jump);
+            if ((long long)__double_as_longlong(hm) > 0 && ((bB ^ bJ) >> 63) && nonzero(B) && nonzero(jump))
+                invb = max_bits(invb, fabs(ca * B * jump) * rwa * recip_pos(g * hm));
+        }
+        const double inv = warp_max(__longlong_as_double((long long)invb));
+        if (lane == 0 && inv > 0.0) atomic_max_pos(&bits[1], inv);
     }
-    inv = warp_max(inv);
-    if (lane == 0 && inv > 0.0) atomic_max_pos(&bits[1], inv);
+    __syncwarp();  // the next element reuses sc
 }
 
 template <int N>
-__global__ void k_dt(DtArgs a) {
+__global__ void __launch_bounds__(32 * DT_WPB) k_dt(DtArgs a) {
+    __shared__ double sc[DT_WPB][(N + 1) * (N + 1)];
     if (stopped(a.stop)) return;
-    const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-    for (long long k = (long long)blockIdx.x * wpb + (threadIdx.x >> 5); k < a.m.K; k += (long long)gridDim.x * wpb)
-        dt_element<N>(a, k, lane);
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+    for (long long k = (long long)blockIdx.x * wpb + w; k < a.m.K; k += (long long)gridDim.x * wpb)
+        dt_element<N>(a, k, lane, sc[w]);
 }
 
 // One thread per instance: dt[i] in use, dt[ninst + i] CFL, dt[2 ninst + i] positivity.
@@ -521,9 +545,8 @@ void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
 
 template <int N>
 void dt_n(swe_ctx* c, const DtArgs& a, cudaStream_t s) {
-    constexpr int WPB = 4;
     Timed tm(c, KC_DT, s);
-    k_dt<N><<<persistent_grid(c, WPB), 32 * WPB, 0, s>>>(a);
+    k_dt<N><<<persistent_grid(c, DT_WPB), 32 * DT_WPB, 0, s>>>(a);
 }
 
 #define SWE_SWITCH_N(N, CALL)                                                         \
