@@ -207,6 +207,48 @@ __device__ __forceinline__ double warp_max(double v) {
     return v;
 }
 
+// Lanes per element of the per-element kernels: the smallest power of two
+// that holds the element's nodes, at most a warp. Small degrees put several
+// elements on one warp (N=1: 8, N=2 and 3: 2), so that the lanes are not idle.
+template <int N>
+constexpr int elem_lanes() {
+    constexpr int nn = (N + 1) * (N + 1);
+    return nn <= 4 ? 4 : (nn <= 8 ? 8 : (nn <= 16 ? 16 : 32));
+}
+
+// Butterfly sum / min over aligned groups of G lanes. For G < 32 the result
+// equals the full-warp butterfly of the same values with zeros (+inf) in the
+// other lanes, bit for bit: those steps only add exact zeros.
+template <int G>
+__device__ __forceinline__ double seg_sum(double v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ double seg_max(double v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ double seg_min(double v) {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+// Any lane of this lane's group of G.
+template <int G>
+__device__ __forceinline__ bool seg_any(bool pred, int lane) {
+    const unsigned b = __ballot_sync(0xffffffffu, pred);
+    if (G == 32) return b != 0u;
+    const unsigned gm = ((1u << G) - 1u) << (lane & ~(G - 1));
+    return (b & gm) != 0u;
+}
+
 // x < 0 (not -0.0) from the bit pattern.
 __device__ __forceinline__ bool is_negative(double x) {
     const unsigned long long b = (unsigned long long)__double_as_longlong(x);
@@ -223,20 +265,23 @@ __device__ __forceinline__ bool below(double x, long long tbits) {
     return (long long)__double_as_longlong(x) < tbits;
 }
 
-template <int N, int MODE>
-__device__ __forceinline__ void update_element(const UpdArgs& a, long long k, int lane) {
-    constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
+// One element on G lanes (sub = the lane's index in its group). Every lane
+// of the warp takes part in the group reductions, also the lanes of a group
+// whose element is past the end (valid false: no loads or stores).
+template <int N, int MODE, int G>
+__device__ __forceinline__ void update_element(const UpdArgs& a, long long k, bool valid, int sub, int lane) {
+    constexpr int n = N + 1, nn = n * n, PER = (nn + G - 1) / G;
     const DeviceMesh& m = a.m;
     const long long KN = m.KN;
-    const double dt = a.dt_dev ? a.dt_dev[m.inst ? m.inst[k] : 0] : a.dt_host;
+    const double dt = !valid ? 0.0 : (a.dt_dev ? a.dt_dev[m.inst ? m.inst[k] : 0] : a.dt_host);
     const double bdt = a.b * dt;
     double h[PER], hu[PER], hv[PER];
     bool neg = false, bad = false;
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        const int node = lane + 32 * r;
+        const int node = sub + G * r;
         h[r] = hu[r] = hv[r] = 0.0;
-        if (node < nn) {
+        if (valid && node < nn) {
             const long long gid = k * nn + node;
             double w0 = a.W[gid], w1 = a.W[KN + gid], w2 = a.W[2 * KN + gid];
             if (MODE == 1) {
@@ -266,18 +311,23 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, in
             bad |= non_finite(w0) || non_finite(w1) || non_finite(w2);
         }
     }
-    bad = __any_sync(0xffffffffu, bad);
-    if (bad && (a.limiter || MODE != 0)) {
-        if (lane == 0) atomicOr(a.status, 2);
-    } else if (a.limiter) {
+    // group decisions; the shuffles below run on all 32 lanes (warp-uniform
+    // branches only), the per-group results are applied under the group's own
+    // flags
+    bad = seg_any<G>(bad, lane);
+    const bool anyneg = seg_any<G>(neg, lane);
+    if (bad && (a.limiter || MODE != 0) && sub == 0) atomicOr(a.status, 2);
+    if (a.limiter) {
+        const bool here = !bad;  // the limiter acts on finite elements
+        const bool need = here && anyneg;
         bool ok = true;
-        if (__any_sync(0xffffffffu, neg)) {
-            // element needs limiting: J-weighted means and minimum
+        if (__any_sync(0xffffffffu, need)) {
+            // an element of this warp needs limiting: J-weighted means and minimum
             double s0 = 0.0, s1 = 0.0, s2 = 0.0, mn = INFINITY;
 #pragma unroll
             for (int r = 0; r < PER; ++r) {
-                const int node = lane + 32 * r;
-                if (node < nn) {
+                const int node = sub + G * r;
+                if (valid && node < nn) {
                     const double wj = m.wJ[k * nn + node];
                     s0 = fma(wj, h[r], s0);
                     s1 = fma(wj, hu[r], s1);
@@ -285,23 +335,25 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, in
                     mn = fmin(mn, h[r]);
                 }
             }
-            const double rv = m.rvol[k];
-            const double m0 = warp_sum(s0) * rv, m1 = warp_sum(s1) * rv, m2 = warp_sum(s2) * rv;
-            mn = warp_min(mn);
-            if (m0 < 0.0) {
-                if (lane == 0) atomicOr(a.status, 1);
-                ok = false;
-            } else if (m0 - mn > 0.0) {
-                const double theta = fmin(1.0, m0 / (m0 - mn));
+            const double rv = valid ? m.rvol[k] : 0.0;
+            const double m0 = seg_sum<G>(s0) * rv, m1 = seg_sum<G>(s1) * rv, m2 = seg_sum<G>(s2) * rv;
+            mn = seg_min<G>(mn);
+            if (need) {
+                if (m0 < 0.0) {
+                    if (sub == 0) atomicOr(a.status, 1);
+                    ok = false;
+                } else if (m0 - mn > 0.0) {
+                    const double theta = fmin(1.0, m0 / (m0 - mn));
 #pragma unroll
-                for (int r = 0; r < PER; ++r) {
-                    h[r] = fma(theta, h[r] - m0, m0);
-                    hu[r] = fma(theta, hu[r] - m1, m1);
-                    hv[r] = fma(theta, hv[r] - m2, m2);
+                    for (int r = 0; r < PER; ++r) {
+                        h[r] = fma(theta, h[r] - m0, m0);
+                        hu[r] = fma(theta, hu[r] - m1, m1);
+                        hv[r] = fma(theta, hv[r] - m2, m2);
+                    }
                 }
             }
         }
-        if (ok) {
+        if (ok && here) {
             const long long tb = __double_as_longlong(a.h_tol);
 #pragma unroll
             for (int r = 0; r < PER; ++r)
@@ -310,8 +362,8 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, in
     }
 #pragma unroll
     for (int r = 0; r < PER; ++r) {
-        const int node = lane + 32 * r;
-        if (node < nn) {
+        const int node = sub + G * r;
+        if (valid && node < nn) {
             const long long gid = k * nn + node;
             a.W[gid] = h[r];
             a.W[KN + gid] = hu[r];
@@ -326,14 +378,19 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, in
     }
 }
 
-// One warp per element, blocks of blockDim.x/32 elements looping over the
-// elements.
+// One element per group of G lanes (32/G elements per warp), blocks of
+// blockDim.x/32 warps looping over the elements.
 template <int N, int MODE>
 __global__ void __launch_bounds__(32 * UPD_MAX_WPB) k_update(UpdArgs a) {
     if (stopped(a.stop)) return;
+    constexpr int G = elem_lanes<N>(), EPW = 32 / G;
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    for (long long k = (long long)blockIdx.x * wpb + wid; k < a.m.K; k += (long long)gridDim.x * wpb)
-        update_element<N, MODE>(a, k, lane);
+    const int sub = lane & (G - 1), grp = lane / G;
+    for (long long kb = ((long long)blockIdx.x * wpb + wid) * EPW; kb < a.m.K;
+         kb += (long long)gridDim.x * wpb * EPW) {
+        const long long k = kb + grp;
+        update_element<N, MODE, G>(a, k, k < a.m.K, sub, lane);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -361,17 +418,19 @@ __device__ __forceinline__ unsigned long long max_bits(unsigned long long a, dou
 
 constexpr int DT_WPB = 4;  // warps (elements) per block of the time-step kernel
 
-// One element on one warp. The celerities c = sqrt(g max(h, 0)) of the CFL
-// part are kept in shared memory (sc, the warp's n*n slots) for the own side
-// of the positivity part. The maxima of non-negative values and the sign
-// tests are integer operations on the bit patterns.
-template <int N>
-__device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lane, double* sc) {
+// One element on a group of G lanes (several elements per warp for small
+// degrees; lanes of a group past the last element only join the
+// shuffles). The celerities c = sqrt(g max(h, 0)) of the CFL part are kept in
+// shared memory (sc, the group's n*n slots) for the own side of the
+// positivity part. The maxima of non-negative values and the sign tests are
+// integer operations on the bit patterns.
+template <int N, int G>
+__device__ __forceinline__ void dt_element(const DtArgs& a, long long k, bool valid, int sub, double* sc) {
     constexpr int n = N + 1, nn = n * n;
     const DeviceMesh& m = a.m;
     const double g = m.g;
     unsigned long long lamb = 0;
-    for (int node = lane; node < nn; node += 32) {
+    for (int node = sub; node < nn && valid; node += G) {
         const long long id = k * nn + node;
         const double h = a.W[id], u = a.uv[id], v = a.uv[m.KN + id];
         const double c = sqrt_pos(g * pos_part(h));
@@ -379,13 +438,13 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
         const double vel = fabs(fma(m.axx[id], u, m.axy[id] * v)) + fabs(fma(m.aex[id], u, m.aey[id] * v));
         lamb = max_bits(lamb, fma(c, a.cfl_n[id], m.rJ[id] * vel));
     }
-    const double lam = warp_max(__longlong_as_double((long long)lamb));
-    unsigned long long* bits = a.bits + 2 * (m.inst ? m.inst[k] : 0);
-    if (lane == 0 && lam > 0.0) atomic_max_pos(&bits[0], lam);
+    const double lam = seg_max<G>(__longlong_as_double((long long)lamb));
+    unsigned long long* bits = a.bits + 2 * (valid && m.inst ? m.inst[k] : 0);
+    if (valid && sub == 0 && lam > 0.0) atomic_max_pos(&bits[0], lam);
     if (a.pos) {  // uniform: the flag is a kernel argument
         __syncwarp();
         unsigned long long invb = 0;
-        for (int sn = lane; sn < 4 * n; sn += 32) {
+        for (int sn = sub; sn < 4 * n && valid; sn += G) {
             const int f = sn / n, p = sn - f * n;
             const int i = (f == 0 || f == 2) ? p : (f == 1 ? N : 0);
             const int j = (f == 1 || f == 3) ? p : (f == 2 ? N : 0);
@@ -413,19 +472,23 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, int lan
             if ((long long)__double_as_longlong(hm) > 0 && ((bB ^ bJ) >> 63) && nonzero(B) && nonzero(jump))
                 invb = max_bits(invb, fabs(ca * B * jump) * rwa * recip_pos(g * hm));
         }
-        const double inv = warp_max(__longlong_as_double((long long)invb));
-        if (lane == 0 && inv > 0.0) atomic_max_pos(&bits[1], inv);
+        const double inv = seg_max<G>(__longlong_as_double((long long)invb));
+        if (valid && sub == 0 && inv > 0.0) atomic_max_pos(&bits[1], inv);
     }
     __syncwarp();  // the next element reuses sc
 }
 
 template <int N>
 __global__ void __launch_bounds__(32 * DT_WPB) k_dt(DtArgs a) {
-    __shared__ double sc[DT_WPB][(N + 1) * (N + 1)];
+    constexpr int G = elem_lanes<N>(), EPW = 32 / G, nn = (N + 1) * (N + 1);
+    __shared__ double sc[DT_WPB][EPW * nn];
     if (stopped(a.stop)) return;
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-    for (long long k = (long long)blockIdx.x * wpb + w; k < a.m.K; k += (long long)gridDim.x * wpb)
-        dt_element<N>(a, k, lane, sc[w]);
+    const int sub = lane & (G - 1), grp = lane / G;
+    for (long long kb = ((long long)blockIdx.x * wpb + w) * EPW; kb < a.m.K; kb += (long long)gridDim.x * wpb * EPW) {
+        const long long k = kb + grp;
+        dt_element<N, G>(a, k, k < a.m.K, sub, sc[w] + grp * nn);
+    }
 }
 
 // One thread per instance: dt[i] in use, dt[ninst + i] CFL, dt[2 ninst + i] positivity.
@@ -536,7 +599,7 @@ __global__ void k_reduce_inst(DeviceMesh m, const double* __restrict__ W, const 
 template <int N>
 void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
     const int wpb = c->upd_wpb;
-    const int blocks = persistent_grid(c, wpb);
+    const int blocks = persistent_grid(c, wpb * (32 / elem_lanes<N>()));
     Timed tm(c, KC_UPDATE, s);
     if (mode == 0) k_update<N, 0><<<blocks, 32 * wpb, 0, s>>>(a);
     else if (mode == 1) k_update<N, 1><<<blocks, 32 * wpb, 0, s>>>(a);
@@ -546,7 +609,7 @@ void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
 template <int N>
 void dt_n(swe_ctx* c, const DtArgs& a, cudaStream_t s) {
     Timed tm(c, KC_DT, s);
-    k_dt<N><<<persistent_grid(c, DT_WPB), 32 * DT_WPB, 0, s>>>(a);
+    k_dt<N><<<persistent_grid(c, DT_WPB * (32 / elem_lanes<N>())), 32 * DT_WPB, 0, s>>>(a);
 }
 
 #define SWE_SWITCH_N(N, CALL)                                                         \
