@@ -104,7 +104,7 @@ def test_lake_at_rest_gpu(N, rot):
     assert np.abs(Wc[1:]).max() < 1e-12
 
 
-@pytest.mark.parametrize("N", [1, 3, 6])
+@pytest.mark.parametrize("N", [1, 2, 3, 6])
 def test_limiter_parity(N):
     p = I.random_rough(N=N, K1=5, seed=40 + N, rotate_seed=N)
     rng = np.random.default_rng(N)
@@ -122,10 +122,13 @@ def test_limiter_parity(N):
     assert np.abs(Wg.cpu().numpy() - Wo).max() < 1e-14
 
 
-def test_limiter_negative_mean_status():
-    p = I.random_smooth(N=3, K1=3, seed=2)
+@pytest.mark.parametrize("N,k", [(3, 4), (1, 5), (2, 3)])
+def test_limiter_negative_mean_status(N, k):
+    """An element with a negative mean sets the status bit, also when it
+    shares a warp with other elements (small N: several elements per warp)."""
+    p = I.random_smooth(N=N, K1=3, seed=2)
     W = p.W.copy()
-    W[0, 4] = -0.5
+    W[0, k] = -0.5
     o, g = pair(p, limiter=True)
     _, rc = o.limit(W)
     Wg = dev(W)
@@ -134,7 +137,7 @@ def test_limiter_negative_mean_status():
     assert g.status() & 1
 
 
-@pytest.mark.parametrize("N,dry", [(2, 0.0), (3, 0.3), (5, 0.2)])
+@pytest.mark.parametrize("N,dry", [(1, 0.2), (2, 0.0), (3, 0.3), (5, 0.2)])
 def test_max_dt_parity(N, dry):
     p = I.random_rough(N=N, K1=5, seed=60 + N, rotate_seed=N, dry_fraction=dry)
     o, g = pair(p, flux=1, limiter=True, cfl=0.4)
