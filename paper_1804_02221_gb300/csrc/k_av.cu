@@ -22,8 +22,9 @@
 //   E_top = S_yxi + S_yeta - (2k+1) B0^2
 //   E_sub = S_zxi - (k+1) B2^2 + S_zeta - (k+1) C0^2 - C2^2
 // which costs O(N^2) per element instead of the O(N^3) transform. One warp
-// evaluates 8 elements at a time, so the per-element reductions are short
-// four-lane butterflies and the scalar work runs on 8 lanes at once.
+// evaluates 8 elements at a time (16 for N = 2, 3 and 32 for N = 1), so the
+// per-element reductions are short butterflies over 4 (2, 1) lanes and the
+// scalar work runs on 8 (16, 32) lanes at once.
 #include <math.h>
 
 #include "kcommon.cuh"
@@ -43,8 +44,15 @@ struct AvArgs {
     const int* stop;
 };
 
-constexpr int AV_EPW = 8;  // elements per warp
 constexpr int AV_WPB = 2;  // warps per block
+
+// Elements per warp: 8 from N = 4 up; more for the small elements of low
+// degree, where the per-element scalar work (the eight sums, epsilon) would
+// otherwise dominate (N = 1: 32, N = 2 and 3: 16).
+template <int N>
+constexpr int av_epw() {
+    return N == 1 ? 32 : (N <= 3 ? 16 : 8);
+}
 
 // epsilon from the nine sums of one element (S_yxi, S_yeta, S_zxi, S_zeta,
 // B0, C0, B2, C2, sum w w Q^2).
@@ -77,6 +85,9 @@ __device__ __forceinline__ double epsilon_from_sums(const double* S, const EpsPa
 // viscous fluxes remain.
 template <int N, bool EPS_GIVEN>
 __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
+    constexpr int AV_EPW = av_epw<N>();
+    constexpr int LPE = 32 / AV_EPW;  // lanes per element for the sums (4, 2 or 1)
+    constexpr int SPL = 8 / LPE;      // projection sums per lane (2, 4 or 8)
     constexpr int n = N + 1, nn = n * n, P4 = 4 * n, PER = (nn + 31) / 32;
     constexpr double iw0 = N * (N + 1) / 2.0;
     __shared__ double sD[nn], sVi[nn], sWW[nn];
@@ -102,7 +113,7 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
     double(*Q)[nn] = sQ[w];
 
     if (!EPS_GIVEN) {
-        // ---- water heights of the 8 elements (contiguous in memory) -------
+        // ---- water heights of the warp's elements (contiguous in memory) --
         // a compile-time trip count, unrolled: the loads of all iterations
         // are in flight together
         constexpr int LQ = (AV_EPW * nn + 31) / 32;
@@ -116,7 +127,7 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
         }
         __syncwarp();
         // ---- the four projections of every element ------------------------
-        // n tasks per lane (AV_EPW * P4 = 32 n), unrolled: the lane's
+        // AV_EPW n / 8 tasks per lane, unrolled: the lane's
         // independent dot products interleave, instead of one dependent chain
         // of fused multiply-adds at a time
         static_assert((AV_EPW * P4) % 32 == 0, "projection tasks fill whole warps");
@@ -134,25 +145,25 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
             for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][b0 + q * st], v);
             sP[w][e][L] = v;
         }
-        // ---- sum w w Q^2: four lanes per element ---------------------------
-        const int e4 = lane >> 2, sub = lane & 3;
+        // ---- sum w w Q^2: LPE lanes per element ----------------------------
+        const int e4 = lane / LPE, sub = lane % LPE;
         double swq = 0.0;
 #pragma unroll
-        for (int r = 0; r < (nn + 3) / 4; ++r) {
-            const int node = sub + 4 * r;
+        for (int r = 0; r < (nn + LPE - 1) / LPE; ++r) {
+            const int node = sub + LPE * r;
             const double q = node < nn ? Q[e4][node] : 0.0;
             swq = fma(sWW[node < nn ? node : 0] * q, q, swq);
         }
-        swq += __shfl_xor_sync(0xffffffffu, swq, 1);
-        swq += __shfl_xor_sync(0xffffffffu, swq, 2);
+#pragma unroll
+        for (int o = 1; o < LPE; o <<= 1) swq += __shfl_xor_sync(0xffffffffu, swq, o);
         __syncwarp();
-        // ---- the eight projection sums: two per lane -----------------------
+        // ---- the eight projection sums: SPL per lane -----------------------
         // sum index m: 0..3 weighted squares of y_xi, y_eta, z_xi, z_eta;
         // 4: B0 = Vinv[N].y_xi, 5: C0 = Vinv[N-1].y_xi, 6: B2 = Vinv[N].z_xi,
         // 7: C2 = Vinv[N-1].z_xi; each written as sum_p (c_p x_p) y_p
 #pragma unroll
-        for (int h2 = 0; h2 < 2; ++h2) {
-            const int mi = 2 * sub + h2;
+        for (int h2 = 0; h2 < SPL; ++h2) {
+            const int mi = SPL * sub + h2;
             const bool sq = mi < 4;
             const double* x = sP[w][e4] + (sq ? mi : (mi < 6 ? 0 : 2)) * n;
             const double* c = sVi + ((mi & 1) == 0 ? N : N - 1) * n;
@@ -251,7 +262,7 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
 
 template <int N>
 void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s, bool eps_given) {
-    const int blocks = grid_for(c->m.K, AV_WPB * AV_EPW);
+    const int blocks = grid_for(c->m.K, AV_WPB * av_epw<N>());
     Timed tm(c, KC_AV, s);
     if (eps_given) k_av<N, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
     else k_av<N, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
