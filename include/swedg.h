@@ -196,6 +196,19 @@ int swe_set_tuning(swe_ctx* ctx, int vol_threads, int upd_warps);
  * stage. Synchronises `stream`; SWE_ERR_NEG_MEAN if the recomputed step
  * fails.
  *
+ * Recorded steps, for a reverse sweep that does not recompute its steps:
+ * swe_adjoint_slots reserves nslots >= 1 step records on the device (each
+ * about 6 S + 2 doubles per node for S = 5 or 3 stages), discarding earlier
+ * records; it synchronises the device. swe_step_record advances W (device,
+ * in place) by one step of swe_step with the given dt > 0 and stores the
+ * step's stage inputs, pre-limit stage results and decisions in record
+ * `slot` (0 <= slot < nslots); W1 is bitwise swe_step's result. It
+ * synchronises `stream`; if the step fails, W is restored to its start
+ * state and SWE_ERR_NEG_MEAN or SWE_ERR_NONFINITE is returned.
+ * swe_step_adjoint_recorded is swe_step_adjoint for the step recorded in
+ * `slot` (same dt), without recomputing it. swe_step_adjoint itself records
+ * its step in slot 0.
+ *
  * swe_gauge_misfit: gauge values h_g = sum over the nodes of element elem[g]
  * of wts[g][node] h (ngauge gauges; wts [ngauge][n*n] are interpolation
  * weights; all device arrays). values (nullable) receives h_g; loss
@@ -204,6 +217,9 @@ int swe_set_tuning(swe_ctx* ctx, int vol_threads, int upd_warps);
  * processed in order by one block (deterministic). Asynchronous. */
 int swe_rhs_adjoint(swe_ctx* ctx, const double* W, const double* Rbar, double* Wbar, double* bbar, void* stream);
 int swe_step_adjoint(swe_ctx* ctx, const double* W0, double dt, double* Wbar, double* bbar, void* stream);
+int swe_adjoint_slots(swe_ctx* ctx, int nslots);
+int swe_step_record(swe_ctx* ctx, double* W, double dt, int slot, void* stream);
+int swe_step_adjoint_recorded(swe_ctx* ctx, int slot, double dt, double* Wbar, double* bbar, void* stream);
 int swe_gauge_misfit(swe_ctx* ctx, const double* W, int ngauge, const int32_t* elem, const double* wts,
                      const double* target, double* values, double* loss, double* Wbar, void* stream);
 

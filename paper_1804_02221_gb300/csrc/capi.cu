@@ -636,36 +636,73 @@ extern "C" int swe_set_tuning(swe_ctx* c, int vol_threads, int upd_warps) {
 
 namespace {
 
+void dev_free(swe_ctx* c, void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < c->allocations.size(); ++i)
+        if (c->allocations[i] == p) {
+            c->allocations.erase(c->allocations.begin() + i);
+            break;
+        }
+    cudaFree(p);
+}
+
+// Step records: nslots sets of the stage data of one step (stage inputs,
+// pre-limit results, viscosities, limiter plans). Replaces earlier records.
+int ensure_slots(swe_ctx* c, int nslots) {
+    swe::AdjWork& A = c->adj;
+    if (A.slots >= nslots) return SWE_OK;
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint: synchronise");
+    dev_free(c, A.Xs);
+    dev_free(c, A.Ys);
+    dev_free(c, A.Es);
+    dev_free(c, A.act);
+    dev_free(c, A.amin);
+    A.Xs = A.Ys = A.Es = nullptr;
+    A.act = A.cut = nullptr;
+    A.amin = nullptr;
+    A.slots = 0;
+    const size_t KN = c->m.KN, K = c->m.K, S = (size_t)A.stages * nslots;
+    A.Xs = dev_alloc(c, S * 3 * KN, e);
+    if (e == cudaSuccess) A.Ys = dev_alloc(c, S * 3 * KN, e);
+    if (e == cudaSuccess) A.Es = dev_alloc(c, S * K, e);
+    void* q = nullptr;
+    if (e == cudaSuccess) e = cudaMalloc(&q, S * (K + KN) + 16);
+    if (e == cudaSuccess) {
+        c->allocations.push_back(q);
+        A.act = static_cast<uint8_t*>(q);
+        A.cut = A.act + S * K;
+        q = nullptr;
+        e = cudaMalloc(&q, sizeof(int32_t) * S * K + 16);
+    }
+    if (e == cudaSuccess) {
+        c->allocations.push_back(q);
+        A.amin = static_cast<int32_t*>(q);
+    }
+    if (e != cudaSuccess) return cuda_fail(e, "adjoint: step records");
+    A.slots = nslots;
+    return SWE_OK;
+}
+
 int ensure_adjoint(swe_ctx* c) {
     swe::AdjWork& A = c->adj;
     if (A.ready) return SWE_OK;
-    const size_t KN = c->m.KN, KS = c->m.KS, K = c->m.K;
-    const int S = 5;  // stages of the longer scheme
+    const size_t KN = c->m.KN, KS = c->m.KS;
     cudaError_t e = cudaSuccess;
 #define ADJ_AL(dst, count)                                                  \
     dst = dev_alloc(c, count, e);                                           \
     if (e != cudaSuccess) return cuda_fail(e, "adjoint: allocation");
     ADJ_AL(A.Ga, 3 * KN) ADJ_AL(A.Guv, 2 * KN) ADJ_AL(A.Gsl, 4 * KS) ADJ_AL(A.Gfo, 3 * KS)
     ADJ_AL(A.GUs, 2 * KS) ADJ_AL(A.Gfvt, 4 * KN) ADJ_AL(A.Gfvo, 2 * KS) ADJ_AL(A.Gfvtr, 4 * KS)
-    ADJ_AL(A.Gsrc, 2 * KN) ADJ_AL(A.Gsrc_acc, 2 * KN) ADJ_AL(A.Khb, 3 * KN) ADJ_AL(A.Rb, 3 * KN) ADJ_AL(A.Wnb, 3 * KN)
-    ADJ_AL(A.Ws, 3 * KN) ADJ_AL(A.Xs, S * 3 * KN) ADJ_AL(A.Ys, S * 3 * KN) ADJ_AL(A.Es, S * K)
+    ADJ_AL(A.Gsrc, 2 * KN) ADJ_AL(A.Gsrc_acc, 2 * KN) ADJ_AL(A.Khb, 3 * KN) ADJ_AL(A.Rb, 3 * KN)
+    ADJ_AL(A.Wnb, 3 * KN) ADJ_AL(A.Ws, 3 * KN)
 #undef ADJ_AL
-    void* q = nullptr;
-    e = cudaMalloc(&q, S * (K + KN) + 16);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint: allocation");
-    c->allocations.push_back(q);
-    A.act = static_cast<uint8_t*>(q);
-    A.cut = A.act + S * K;
-    q = nullptr;
-    e = cudaMalloc(&q, sizeof(int32_t) * S * K + 16);
-    if (e != cudaSuccess) return cuda_fail(e, "adjoint: allocation");
-    c->allocations.push_back(q);
-    A.amin = static_cast<int32_t*>(q);
+    A.stages = 5;  // stages of the longer scheme
+    if (int rc = ensure_slots(c, 1)) return rc;
     // wall slots of the side-node viscous cotangents are never written
     e = cudaMemset(A.Gfvtr, 0, sizeof(double) * 4 * KS);
     if (e == cudaSuccess) e = cudaDeviceSynchronize();
     if (e != cudaSuccess) return cuda_fail(e, "adjoint: initialisation");
-    A.stages = S;
     A.ready = true;
     return SWE_OK;
 }
@@ -697,35 +734,70 @@ extern "C" int swe_rhs_adjoint(swe_ctx* c, const double* W, const double* Rbar, 
     return check_launch("swe_rhs_adjoint");
 }
 
-extern "C" int swe_step_adjoint(swe_ctx* c, const double* W0, double dt, double* Wbar, double* bbar,
-                                void* stream) {
-    if (int rc = adjoint_args(c, W0, W0, Wbar, "swe_step_adjoint")) return rc;
-    if (!(dt > 0.0)) return fail(SWE_ERR_ARG, "swe_step_adjoint: dt must be the step's positive size");
-    cudaStream_t s = (cudaStream_t)stream;
+namespace {
+
+// One step of size dt on W (advanced in place) with the stage inputs, the
+// pre-limit stage results, the viscosities and the limiter's plans stored in
+// record `slot`. The same kernels and arithmetic as swe_step's, so W1 is
+// bitwise swe_step's result (the limiter runs separately to record its plan,
+// with the fused update's arithmetic). On failure W is restored from the
+// record (its first stage input) and the status error is returned.
+int record_step(swe_ctx* c, double* W, double dt, int slot, cudaStream_t s, const char* where) {
     swe::AdjWork& A = c->adj;
     const long long KN = c->m.KN, K = c->m.K, n3 = 3 * KN;
-    const int stages = c->p.rk == 0 ? 5 : 3;
+    const int stages = c->p.rk == 0 ? 5 : 3, S = A.stages;
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     const int lim = c->p.limiter;
+    double* Xs = A.Xs + (size_t)slot * S * n3;
+    double* Ys = A.Ys + (size_t)slot * S * n3;
+    double* Es = A.Es + (size_t)slot * S * K;
+    uint8_t* act = A.act + (size_t)slot * S * K;
+    uint8_t* cut = A.cut + (size_t)slot * S * KN;
+    int32_t* amin = A.amin + (size_t)slot * S * K;
     cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
-    // ---- forward recomputation with the decisions recorded ----
-    cudaMemcpyAsync(A.Ws, W0, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    if (c->p.rk == 1) cudaMemcpyAsync(c->w.Wn, W0, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-    swe::launch_prim(c, A.Ws, s, nullptr);
+    if (c->p.rk == 1) cudaMemcpyAsync(c->w.Wn, W, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    swe::launch_prim(c, W, s, nullptr);
     for (int st = 0; st < stages; ++st) {
-        cudaMemcpyAsync(A.Xs + st * n3, A.Ws, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        swe::rhs_chain(c, A.Ws, c->w.R, s, nullptr, true);
-        cudaMemcpyAsync(A.Es + st * K, c->w.eps, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaMemcpyAsync(Xs + st * n3, W, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        swe::rhs_chain(c, W, c->w.R, s, nullptr, true);
+        cudaMemcpyAsync(Es + st * K, c->w.eps, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
         c->p.limiter = 0;  // the limiter runs separately, recording its plan
         if (c->p.rk == 0)
-            swe::launch_update(c, 1, A.Ws, kLsrkA[st], kLsrkB[st], dt, nullptr, s, nullptr, true);
+            swe::launch_update(c, 1, W, kLsrkA[st], kLsrkB[st], dt, nullptr, s, nullptr, true);
         else
-            swe::launch_update(c, 2, A.Ws, ca[st], cb[st], dt, nullptr, s, nullptr, true);
+            swe::launch_update(c, 2, W, ca[st], cb[st], dt, nullptr, s, nullptr, true);
         c->p.limiter = lim;
-        cudaMemcpyAsync(A.Ys + st * n3, A.Ws, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
-        if (lim) swe::launch_limit_record(c, A.Ws, A.act + st * K, A.amin + st * K, A.cut + st * KN, s);
+        cudaMemcpyAsync(Ys + st * n3, W, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        if (lim) swe::launch_limit_record(c, W, act + st * K, amin + st * K, cut + st * KN, s);
     }
-    // ---- reverse sweep ----
+    if (int rc = check_launch(where)) return rc;
+    int status = 0;
+    cudaMemcpyAsync(&status, c->w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, where);
+    if (status) {
+        cudaMemcpyAsync(W, Xs, n3 * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        cudaStreamSynchronize(s);
+        return fail((status & 2) ? SWE_ERR_NONFINITE : SWE_ERR_NEG_MEAN,
+                    std::string(where) + ": the step failed (status bits set); W restored");
+    }
+    return SWE_OK;
+}
+
+// The reverse sweep of the step recorded in `slot` (size dt): Wbar becomes
+// the cotangent of the step's start state; the bathymetry cotangent is added
+// to bbar (nullable).
+int reverse_step(swe_ctx* c, int slot, double dt, double* Wbar, double* bbar, cudaStream_t s, const char* where) {
+    swe::AdjWork& A = c->adj;
+    const long long KN = c->m.KN, K = c->m.K, n3 = 3 * KN;
+    const int stages = c->p.rk == 0 ? 5 : 3, S = A.stages;
+    const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
+    const double* Xs = A.Xs + (size_t)slot * S * n3;
+    const double* Ys = A.Ys + (size_t)slot * S * n3;
+    const double* Es = A.Es + (size_t)slot * S * K;
+    const uint8_t* act = A.act + (size_t)slot * S * K;
+    const uint8_t* cut = A.cut + (size_t)slot * S * KN;
+    const int32_t* amin = A.amin + (size_t)slot * S * K;
     cudaMemsetAsync(A.Khb, 0, n3 * sizeof(double), s);
     if (c->p.rk == 1) cudaMemsetAsync(A.Wnb, 0, n3 * sizeof(double), s);
     // the stages' source-coefficient cotangents are summed and carried to
@@ -733,23 +805,57 @@ extern "C" int swe_step_adjoint(swe_ctx* c, const double* W0, double dt, double*
     if (bbar) cudaMemsetAsync(A.Gsrc_acc, 0, 2 * KN * sizeof(double), s);
     for (int st = stages - 1; st >= 0; --st) {
         const double a = c->p.rk == 0 ? kLsrkA[st] : ca[st], b = c->p.rk == 0 ? kLsrkB[st] : cb[st];
-        swe::launch_update_adjoint(c, c->p.rk == 0 ? 1 : 2, Wbar, A.Ys + st * n3, A.act + st * K, A.amin + st * K,
-                                   A.cut + st * KN, A.Khb, A.Rb, A.Wnb, a, b, dt, s);
-        const double* X = A.Xs + st * n3;
-        cudaMemcpyAsync(c->w.eps, A.Es + st * K, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        swe::launch_update_adjoint(c, c->p.rk == 0 ? 1 : 2, Wbar, Ys + st * n3, act + st * K, amin + st * K,
+                                   cut + st * KN, A.Khb, A.Rb, A.Wnb, a, b, dt, s);
+        const double* X = Xs + st * n3;
+        cudaMemcpyAsync(c->w.eps, Es + st * K, K * sizeof(double), cudaMemcpyDeviceToDevice, s);
         adjoint_prerequisites(c, X, s, true);
         swe::launch_rhs_adjoint(c, X, A.Rb, Wbar, bbar, s, true);
     }
     if (bbar) swe::launch_src_adjoint(c, A.Gsrc_acc, bbar, s);
     if (c->p.rk == 1) swe::launch_axpy(c, n3, 1.0, A.Wnb, Wbar, s);
-    int rc = check_launch("swe_step_adjoint");
-    if (rc) return rc;
-    int status = 0;
-    cudaMemcpyAsync(&status, c->w.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+    if (int rc = check_launch(where)) return rc;
     cudaError_t e = cudaStreamSynchronize(s);
-    if (e != cudaSuccess) return cuda_fail(e, "swe_step_adjoint");
-    if (status) return fail(SWE_ERR_NEG_MEAN, "swe_step_adjoint: the recomputed step failed (status bits set)");
+    if (e != cudaSuccess) return cuda_fail(e, where);
     return SWE_OK;
+}
+
+}  // namespace
+
+extern "C" int swe_step_adjoint(swe_ctx* c, const double* W0, double dt, double* Wbar, double* bbar,
+                                void* stream) {
+    if (int rc = adjoint_args(c, W0, W0, Wbar, "swe_step_adjoint")) return rc;
+    if (!(dt > 0.0)) return fail(SWE_ERR_ARG, "swe_step_adjoint: dt must be the step's positive size");
+    cudaStream_t s = (cudaStream_t)stream;
+    swe::AdjWork& A = c->adj;
+    // the step is recomputed from a copy of W0, recorded in slot 0
+    cudaMemcpyAsync(A.Ws, W0, 3 * c->m.KN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+    if (int rc = record_step(c, A.Ws, dt, 0, s, "swe_step_adjoint"))
+        return rc == SWE_ERR_CUDA ? rc : fail(SWE_ERR_NEG_MEAN, "swe_step_adjoint: the recomputed step failed");
+    return reverse_step(c, 0, dt, Wbar, bbar, s, "swe_step_adjoint");
+}
+
+extern "C" int swe_adjoint_slots(swe_ctx* c, int nslots) {
+    if (!c || nslots < 1) return fail(SWE_ERR_ARG, "swe_adjoint_slots: bad argument");
+    if (c->p.volume != 0)
+        return fail(SWE_ERR_ARG, "swe_adjoint_slots: the adjoint covers the split (entropy-stable) form only");
+    if (int rc = ensure_adjoint(c)) return rc;
+    return ensure_slots(c, nslots);
+}
+
+extern "C" int swe_step_record(swe_ctx* c, double* W, double dt, int slot, void* stream) {
+    if (int rc = adjoint_args(c, W, W, W, "swe_step_record")) return rc;
+    if (!(dt > 0.0)) return fail(SWE_ERR_ARG, "swe_step_record: dt must be positive");
+    if (slot < 0 || slot >= c->adj.slots) return fail(SWE_ERR_ARG, "swe_step_record: slot out of range");
+    return record_step(c, W, dt, slot, (cudaStream_t)stream, "swe_step_record");
+}
+
+extern "C" int swe_step_adjoint_recorded(swe_ctx* c, int slot, double dt, double* Wbar, double* bbar,
+                                         void* stream) {
+    if (int rc = adjoint_args(c, Wbar, Wbar, Wbar, "swe_step_adjoint_recorded")) return rc;
+    if (!(dt > 0.0)) return fail(SWE_ERR_ARG, "swe_step_adjoint_recorded: dt must be the step's positive size");
+    if (slot < 0 || slot >= c->adj.slots) return fail(SWE_ERR_ARG, "swe_step_adjoint_recorded: slot out of range");
+    return reverse_step(c, slot, dt, Wbar, bbar, (cudaStream_t)stream, "swe_step_adjoint_recorded");
 }
 
 extern "C" int swe_gauge_misfit(swe_ctx* c, const double* W, int ngauge, const int32_t* elem, const double* wts,

@@ -157,12 +157,14 @@ struct AdjWork {
     double* Rb = nullptr;     // [3][KN] right-hand-side cotangent of a stage
     double* Wnb = nullptr;    // [3][KN] step-start cotangent (SSP)
     double* Ws = nullptr;     // [3][KN] recomputed state
-    double* Xs = nullptr;     // [stages][3][KN] stage inputs
-    double* Ys = nullptr;     // [stages][3][KN] pre-limit stage results
-    double* Es = nullptr;     // [stages][K] element viscosities
-    uint8_t* act = nullptr;   // [stages][K] limited elements
-    int32_t* amin = nullptr;  // [stages][K] node of the minimum
-    uint8_t* cut = nullptr;   // [stages][KN] h_tol cut
+    // step records, [slots] of: (the stage data of one recorded step)
+    int slots = 0;
+    double* Xs = nullptr;     // [slots][stages][3][KN] stage inputs
+    double* Ys = nullptr;     // [slots][stages][3][KN] pre-limit stage results
+    double* Es = nullptr;     // [slots][stages][K] element viscosities
+    uint8_t* act = nullptr;   // [slots][stages][K] limited elements
+    int32_t* amin = nullptr;  // [slots][stages][K] node of the minimum
+    uint8_t* cut = nullptr;   // [slots][stages][KN] h_tol cut
 };
 
 }  // namespace swe

@@ -25,7 +25,8 @@ SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "s
            "swe_ens_create", "swe_ens_destroy", "swe_ens_size", "swe_ens_layout", "swe_ens_rhs",
            "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches", "swe_autotune",
            "swe_get_tuning", "swe_set_tuning", "swe_ens_autotune", "swe_ens_group", "swe_rhs_adjoint",
-           "swe_step_adjoint", "swe_gauge_misfit"]
+           "swe_step_adjoint", "swe_adjoint_slots", "swe_step_record", "swe_step_adjoint_recorded",
+           "swe_gauge_misfit"]
 
 
 class Params(ctypes.Structure):
@@ -104,6 +105,9 @@ def lib():
     L.swe_ens_group.argtypes = [vp, ctypes.c_int, ip, ip, ip, ip]
     L.swe_rhs_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
     L.swe_step_adjoint.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
+    L.swe_adjoint_slots.argtypes = [vp, ctypes.c_int]
+    L.swe_step_record.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp]
+    L.swe_step_adjoint_recorded.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp, vp, vp]
     L.swe_gauge_misfit.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
     L.swe_last_error.argtypes = []
     L.swe_last_error.restype = ctypes.c_char_p
@@ -270,6 +274,21 @@ class SweContext:
         step's bathymetry cotangent is added to bbar (if given)."""
         _check(lib().swe_step_adjoint(self._h, self._state(W0), float(dt), self._state(Wbar), self._plane(bbar),
                                       _stream(stream)))
+        return Wbar
+
+    def adjoint_slots(self, nslots):
+        """Reserve nslots step records (swe_adjoint_slots)."""
+        _check(lib().swe_adjoint_slots(self._h, int(nslots)))
+
+    def step_record(self, W, dt, slot, stream=None):
+        """One step of size dt on W in place, recorded in `slot` (swe_step_record)."""
+        _check(lib().swe_step_record(self._h, self._state(W), float(dt), int(slot), _stream(stream)))
+        return W
+
+    def step_adjoint_recorded(self, slot, dt, Wbar, bbar=None, stream=None):
+        """swe_step_adjoint for the step recorded in `slot`."""
+        _check(lib().swe_step_adjoint_recorded(self._h, int(slot), float(dt), self._state(Wbar), self._plane(bbar),
+                                               _stream(stream)))
         return Wbar
 
     def gauge_misfit(self, W, elem, wts, target=None, values=None, loss=None, Wbar=None, stream=None):
@@ -439,8 +458,13 @@ class GaugeLoss:
                 self.ckpt[t + 1] = W.clone()
         return loss[0]
 
-    def backward(self, grad_b=True):
-        """(dL/dW0, dL/db) of the last forward run."""
+    def backward(self, grad_b=True, recorded=True):
+        """(dL/dW0, dL/db) of the last forward run. Each segment between
+        checkpoints is recomputed once; with `recorded` its steps are
+        recorded on the way (swe_step_record, one record per step of the
+        segment) so that the reverse sweep does not recompute them again,
+        otherwise every step adjoint recomputes its step (swe_step_adjoint).
+        Both give the same gradients bit for bit."""
         import torch
         ctx = self.ctx
         W0 = self.ckpt[0]
@@ -448,6 +472,8 @@ class GaugeLoss:
         bbar = torch.zeros((ctx.K, ctx.n, ctx.n), dtype=torch.float64, device=W0.device) if grad_b else None
         T = self.nsteps
         starts = sorted(self.ckpt)
+        if recorded:
+            ctx.adjoint_slots(min(self.checkpoint, T))
         for c0 in reversed(starts):
             nxt = [s for s in starts if s > c0]
             c1 = nxt[0] if nxt else T
@@ -455,11 +481,17 @@ class GaugeLoss:
             states = [self.ckpt[c0].clone()]
             for t in range(c0, c1):
                 W = states[-1].clone()
-                ctx.step(W, self.dts[t], 1)
+                if recorded:
+                    ctx.step_record(W, self.dts[t], t - c0)
+                else:
+                    ctx.step(W, self.dts[t], 1)
                 states.append(W)
             for t in range(c1, c0, -1):
                 ctx.gauge_misfit(states[t - c0], self.elem, self.wts, target=self.targets[t - 1], Wbar=Wbar)
-                ctx.step_adjoint(states[t - 1 - c0], self.dts[t - 1], Wbar, bbar)
+                if recorded:
+                    ctx.step_adjoint_recorded(t - 1 - c0, self.dts[t - 1], Wbar, bbar)
+                else:
+                    ctx.step_adjoint(states[t - 1 - c0], self.dts[t - 1], Wbar, bbar)
         return Wbar, bbar
 
 
