@@ -139,6 +139,18 @@ int swe_entropy(swe_ctx* ctx, const double* W, double* E, void* stream);
 /* Both in one pass: out4 = (mass, x momentum, y momentum, entropy), host. */
 int swe_integrals(swe_ctx* ctx, const double* W, double* out4, void* stream);
 
+/* Discrete entropy rate of device state W (Sec. 2: the entropy variables
+ * q = (g(h+b) - (u^2+v^2)/2, u, v) of Eq. entropyVariables contracted with
+ * the semi-discrete operator): rate = sum_k sum_ij J w_i w_j q(W_ij).R_ij
+ * with R = swe_rhs(W), the time derivative of swe_entropy along the
+ * semi-discrete flow (zero up to rounding for the entropy-conservative
+ * flux on a periodic or walled mesh without viscosity, <= 0 for the
+ * entropy-stable flux and the artificial viscosity). scale (host, nullable)
+ * receives sum J w_i w_j sum_c |q_c R_c|, the size of the terms that cancel.
+ * Evaluates R into the context's work buffer (not during a step);
+ * synchronises `stream`. */
+int swe_entropy_rate(swe_ctx* ctx, const double* W, double* rate, double* scale, void* stream);
+
 /* Copy the element viscosities epsilon_k (App. A) of the last swe_rhs into
  * device array eps[K]. Asynchronous. */
 int swe_get_epsilon(swe_ctx* ctx, double* eps, void* stream);

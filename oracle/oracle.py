@@ -68,6 +68,7 @@ def lib():
         L.orc_step.argtypes = [vp, dp, ctypes.c_double, ctypes.c_int, dp]
         L.orc_mass.argtypes = [vp, dp, dp]
         L.orc_entropy.argtypes = [vp, dp, dp]
+        L.orc_entropy_rate.argtypes = [vp, dp, dp, dp]
         L.orc_volume_flux.argtypes = [ctypes.c_double, dp, dp, dp, dp]
         L.orc_volume_flux.restype = None
         L.orc_surface_flux.argtypes = [ctypes.c_double, ctypes.c_int, dp, dp, ctypes.c_double,
@@ -207,6 +208,13 @@ class Oracle:
         out = np.zeros(3)
         lib().orc_mass(self._h, _p(self._W(W)), _p(out))
         return out
+
+    def entropy_rate(self, W):
+        """(rate, scale): sum J w w q(W).R(W) and sum J w w |q_c R_c|."""
+        r, sc = ctypes.c_double(), ctypes.c_double()
+        rc = lib().orc_entropy_rate(self._h, _p(self._W(W)), ctypes.byref(r), ctypes.byref(sc))
+        assert rc == OK
+        return r.value, sc.value
 
     def entropy(self, W):
         e = ctypes.c_double()

@@ -1083,6 +1083,41 @@ int orc_entropy(const orc_mesh* m, const double* W, double* E) {
     return ORC_OK;
 }
 
+/* Discrete entropy rate: sum J w_i w_j q(W_ij) . R_ij with the entropy
+ * variables q = (g(h+b) - (u^2+v^2)/2, u, v) of Eq. entropyVariables and
+ * R = orc_rhs(W) (Sec. 2: the entropy function contracted with the
+ * semi-discrete time derivative). scale (nullable) receives
+ * sum J w_i w_j sum_c |q_c R_c|. */
+int orc_entropy_rate(orc_mesh* m, const double* W, double* rate, double* scale) {
+    if (!m || !W || !rate) return ORC_ERR_ARG;
+    int n = m->n;
+    size_t nn = (size_t)m->K * n * n;
+    double* R = (double*)malloc(3 * nn * sizeof(double));
+    if (!R) return ORC_ERR_ARG;
+    int rc = orc_rhs(m, W, R);
+    if (rc != ORC_OK) {
+        free(R);
+        return rc;
+    }
+    double s = 0.0, a = 0.0;
+    for (int k = 0; k < m->K; ++k)
+        for (int j = 0; j < n; ++j)
+            for (int i = 0; i < n; ++i) {
+                size_t id = nid(m, k, i, j);
+                double h = W[id], u = velocity(h, W[nn + id]), v = velocity(h, W[2 * nn + id]);
+                double q[3] = {m->g * (h + m->b[id]) - 0.5 * (u * u + v * v), u, v};
+                double wJ = m->w[i] * m->w[j] * m->J[id];
+                for (int c = 0; c < 3; ++c) {
+                    s += wJ * q[c] * R[c * nn + id];
+                    a += wJ * fabs(q[c] * R[c * nn + id]);
+                }
+            }
+    free(R);
+    *rate = s;
+    if (scale) *scale = a;
+    return ORC_OK;
+}
+
 int orc_threads(void) {
 #ifdef _OPENMP
     return omp_get_max_threads();

@@ -78,6 +78,9 @@ int orc_step(orc_mesh* m, double* W, double dt, int nsteps, double* dt_last);
 
 int orc_mass(const orc_mesh* m, const double* W, double* out3);
 int orc_entropy(const orc_mesh* m, const double* W, double* E);
+/* Discrete entropy rate sum J w w q(W).R(W) (entropy variables of Eq.
+ * entropyVariables, R = orc_rhs(W)); scale (nullable): sum J w w |q_c R_c|. */
+int orc_entropy_rate(orc_mesh* m, const double* W, double* rate, double* scale);
 
 /* Pointwise fluxes (for the flux pins). */
 void orc_volume_flux(double g, const double* Wa, const double* Wb, double* Fs, double* Gs);

@@ -893,6 +893,19 @@ extern "C" int swe_entropy(swe_ctx* c, const double* W, double* E, void* stream)
     return check_launch("swe_entropy");
 }
 
+extern "C" int swe_entropy_rate(swe_ctx* c, const double* W, double* rate, double* scale, void* stream) {
+    if (!c || !W || !rate) return fail(SWE_ERR_ARG, "swe_entropy_rate: NULL argument");
+    cudaStream_t s = (cudaStream_t)stream;
+    swe::rhs_chain(c, W, c->w.R, s, nullptr, false);
+    double h[4];
+    swe::launch_rate(c, W, c->w.R, h, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_entropy_rate");
+    *rate = h[0];
+    if (scale) *scale = h[1];
+    return check_launch("swe_entropy_rate");
+}
+
 extern "C" int swe_integrals(swe_ctx* c, const double* W, double* out4, void* stream) {
     if (!c || !W || !out4) return fail(SWE_ERR_ARG, "swe_integrals: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;

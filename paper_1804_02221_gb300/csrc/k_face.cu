@@ -556,6 +556,41 @@ __global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int wh
         for (int c = 0; c < 4; ++c) part[c * RED_BLOCKS + blockIdx.x] = sh[c][0];
 }
 
+// Discrete entropy rate: per-block partial sums of J w_i w_j q(W) . R with
+// the entropy variables q = (g(h+b) - (u^2+v^2)/2, u, v) of Eq.
+// entropyVariables (component 0), and of J w_i w_j sum_c |q_c R_c| (component
+// 1, the scale of the cancellation); components 2 and 3 are zero.
+__global__ void k_rate_part(DeviceMesh m, const double* __restrict__ W, const double* __restrict__ R,
+                            double* __restrict__ part) {
+    __shared__ double sh[2][RED_THREADS];
+    double s0 = 0.0, s1 = 0.0;
+    const double g = m.g;
+    for (long long id = blockIdx.x * (long long)blockDim.x + threadIdx.x; id < m.KN;
+         id += (long long)gridDim.x * blockDim.x) {
+        const double wj = m.wJ[id], h = W[id];
+        double u, v;
+        velocities(h, W[m.KN + id], W[2 * m.KN + id], u, v);
+        const double q1 = fma(g, h + m.bn[id], -0.5 * fma(u, u, v * v));
+        const double t1 = q1 * R[id], t2 = u * R[m.KN + id], t3 = v * R[2 * m.KN + id];
+        s0 = fma(wj, t1 + t2 + t3, s0);
+        s1 = fma(wj, fabs(t1) + fabs(t2) + fabs(t3), s1);
+    }
+    sh[0][threadIdx.x] = s0;
+    sh[1][threadIdx.x] = s1;
+    __syncthreads();
+    for (int o = RED_THREADS / 2; o > 0; o >>= 1) {
+        if ((int)threadIdx.x < o)
+            for (int c = 0; c < 2; ++c) sh[c][threadIdx.x] += sh[c][threadIdx.x + o];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[blockIdx.x] = sh[0][0];
+        part[RED_BLOCKS + blockIdx.x] = sh[1][0];
+        part[2 * RED_BLOCKS + blockIdx.x] = 0.0;
+        part[3 * RED_BLOCKS + blockIdx.x] = 0.0;
+    }
+}
+
 // One warp per component: lane sums of a fixed stride, then a fixed butterfly.
 __global__ void k_reduce_final(const double* __restrict__ part, double* __restrict__ out) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -686,6 +721,18 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
     {
         Timed tm(c, KC_REDUCE, s);
         k_reduce_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->m, W, what, c->w.part);
+    }
+    {
+        Timed tm(c, KC_REDUCE, s);
+        k_reduce_final<<<1, 128, 0, s>>>(c->w.part, c->w.part + 4 * RED_BLOCKS);
+    }
+    cudaMemcpyAsync(host_out, c->w.part + 4 * RED_BLOCKS, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+void launch_rate(swe_ctx* c, const double* W, const double* R, double* host_out, cudaStream_t s) {
+    {
+        Timed tm(c, KC_REDUCE, s);
+        k_rate_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->m, W, R, c->w.part);
     }
     {
         Timed tm(c, KC_REDUCE, s);

@@ -237,6 +237,8 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
 // Per-instance (mass, momenta, entropy) of an ensemble group into device
 // out[4 * ninst]; ebeg (device, ninst + 1) holds the element ranges.
 void launch_reduce_inst(swe_ctx* c, const double* W, const long long* ebeg, double* out, cudaStream_t s);
+// host_out[0] = sum J w w q(W).R, host_out[1] = sum J w w |q_c R_c| (asynchronous copy)
+void launch_rate(swe_ctx* c, const double* W, const double* R, double* host_out, cudaStream_t s);
 
 // One right-hand side R(W) (prim_done: the velocities of W are already in
 // the work buffer, written by the previous stage update; eps_done: so are its

@@ -26,7 +26,7 @@ SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "s
            "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches", "swe_autotune",
            "swe_get_tuning", "swe_set_tuning", "swe_ens_autotune", "swe_ens_group", "swe_rhs_adjoint",
            "swe_step_adjoint", "swe_adjoint_slots", "swe_step_record", "swe_step_adjoint_recorded",
-           "swe_gauge_misfit"]
+           "swe_gauge_misfit", "swe_entropy_rate"]
 
 
 class Params(ctypes.Structure):
@@ -106,6 +106,7 @@ def lib():
     L.swe_rhs_adjoint.argtypes = [vp, vp, vp, vp, vp, vp]
     L.swe_step_adjoint.argtypes = [vp, vp, ctypes.c_double, vp, vp, vp]
     L.swe_adjoint_slots.argtypes = [vp, ctypes.c_int]
+    L.swe_entropy_rate.argtypes = [vp, vp, dp, dp, vp]
     L.swe_step_record.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp]
     L.swe_step_adjoint_recorded.argtypes = [vp, ctypes.c_int, ctypes.c_double, vp, vp, vp]
     L.swe_gauge_misfit.argtypes = [vp, vp, ctypes.c_int, vp, vp, vp, vp, vp, vp, vp]
@@ -217,6 +218,12 @@ class SweContext:
         e = ctypes.c_double()
         _check(lib().swe_entropy(self._h, self._state(W), ctypes.byref(e), _stream(stream)))
         return e.value
+
+    def entropy_rate(self, W, stream=None):
+        """(rate, scale): sum J w w q(W).R(W) and sum J w w |q_c R_c|."""
+        r, sc = ctypes.c_double(), ctypes.c_double()
+        _check(lib().swe_entropy_rate(self._h, self._state(W), ctypes.byref(r), ctypes.byref(sc), _stream(stream)))
+        return r.value, sc.value
 
     def integrals(self, W, stream=None):
         """(mass, x momentum, y momentum, entropy) in one pass."""
@@ -405,6 +412,12 @@ class SweEnsemble:
         if raise_on_error:
             _check(rc)
         return rc, np.array(dl[:])
+
+    def entropy_rate(self, W, stream=None):
+        """(rate, scale): sum J w w q(W).R(W) and sum J w w |q_c R_c|."""
+        r, sc = ctypes.c_double(), ctypes.c_double()
+        _check(lib().swe_entropy_rate(self._h, self._state(W), ctypes.byref(r), ctypes.byref(sc), _stream(stream)))
+        return r.value, sc.value
 
     def integrals(self, W, stream=None):
         out = (ctypes.c_double * (4 * self.ninst))()

@@ -328,3 +328,34 @@ def test_step_full_size_dam_break_N7():
     assert rco == 0 and rcg == 0
     assert abs(dtg - dto) < 1e-13 * dto
     assert rel(Wg.cpu().numpy(), Wo) < STEP_TOL
+
+
+@pytest.mark.parametrize("N,flux,av", [(1, 0, False), (3, 1, True), (4, 0, False), (7, 1, True)])
+def test_entropy_rate_parity(N, flux, av):
+    """swe_entropy_rate against the oracle's rate; for the entropy-conservative
+    scheme without viscosity the GPU's rate vanishes to rounding itself."""
+    p = I.random_rough(N=N, K1=4, seed=80 + N, rotate_seed=N)
+    kw = dict(flux=flux, av=av, eps0=0.03, sigma_min=-6.0, sigma_max=-0.5)
+    o, g = pair(p, **kw)
+    ro, so = o.entropy_rate(p.W)
+    rg, sg = g.entropy_rate(dev(p.W))
+    assert abs(rg - ro) < 1e-11 * so
+    assert abs(sg - so) < 1e-11 * so
+    if flux == 0 and not av:
+        assert abs(rg) < 1e-13 * sg
+    else:
+        assert rg < 0
+
+
+def test_entropy_rate_full_size_dam_break_N7():
+    """The benchmark workload two steps after the dam release (at t = 0 the
+    water is at rest and the rate is exactly zero on both sides)."""
+    p = I.dam_break(N=7)
+    kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    o, g = pair(p, **kw)
+    W, rc, _ = o.step(p.W, 0.0, 2)
+    assert rc == 0
+    ro, so = o.entropy_rate(W)
+    rg, sg = g.entropy_rate(dev(W))
+    assert so > 0 and rg < 0
+    assert abs(rg - ro) < 1e-11 * so
