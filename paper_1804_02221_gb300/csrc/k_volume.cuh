@@ -24,6 +24,9 @@
 //    -(u_i Q + P Sx) at node q; after both lines the node adds u A1 (and
 //    v A1) and doubles A1. One pair is then 15 FP64 instructions (4 for Q,
 //    1 for P, 2 for the mass sums, 8 fused multiply-adds for the momenta).
+//    From N = 5 up the pressure parts P Sx = p_i (h_q Sx) are summed per
+//    node as h_q Sx (B2, B3) and scaled by the node's p = 2g h once per line:
+//    14 per pair.
 //  * One thread per element line: it runs its xi-line, hands the results
 //    through shared memory, then runs the eta-line with the same index
 //    starting from them, and finishes the nodes of that column (interface
@@ -88,6 +91,14 @@ constexpr int vol_min_blocks() {
     return b > 0 ? b : 1;
 }
 
+// Pressure parts of the pair fluxes summed per node (14 FP64 instructions
+// per pair and 4 per node instead of 15 per pair): a gain from N = 5 up
+// (measured; at N = 3 the per-node products cost more than the pairs save).
+template <int N>
+constexpr bool vol_pressure_sums() {
+    return N >= 5;
+}
+
 template <int N>
 __host__ __device__ constexpr int pair_index(int i, int q) {
     return i * (N + 1) - i * (i + 1) / 2 + (q - i - 1);
@@ -100,7 +111,7 @@ __host__ __device__ constexpr int pair_index(int i, int q) {
 template <int N, int BLK>
 __device__ __forceinline__ void pair_loop(const double* __restrict__ s, int base, int stride,
                                           const double* __restrict__ pmk, double* A1, double* A2,
-                                          double* A3) {
+                                          double* A3, double* B2, double* B3) {
     constexpr int n = N + 1;
     const double* sH = s + F_H * BLK;
     const double* sHU = s + F_HU * BLK;
@@ -111,20 +122,36 @@ __device__ __forceinline__ void pair_loop(const double* __restrict__ s, int base
 #pragma unroll
     for (int i = 0; i < n; ++i) {
         const int ni = base + i * stride;
-        const double hu_i = sHU[ni], hv_i = sHV[ni], u_i = sU[ni], v_i = sV[ni], p_i = sP[ni];
+        const double hu_i = sHU[ni], hv_i = sHV[ni], u_i = sU[ni], v_i = sV[ni];
+        const double h_i = sH[ni], p_i = sP[ni];
 #pragma unroll
         for (int q = i + 1; q < n; ++q) {
             const int nq = base + q * stride;
             const int pr = pair_index<N>(i, q);
             const double2 c = __ldg(reinterpret_cast<const double2*>(pmk + 2 * pr * n));
             const double Q = fma(hu_i + sHU[nq], c.x, (hv_i + sHV[nq]) * c.y);
-            const double P = p_i * sH[nq];
             A1[i] += Q;
             A1[q] -= Q;
-            A2[i] = fma(P, c.x, fma(sU[nq], Q, A2[i]));
-            A2[q] = fma(-P, c.x, fma(-u_i, Q, A2[q]));
-            A3[i] = fma(P, c.y, fma(sV[nq], Q, A3[i]));
-            A3[q] = fma(-P, c.y, fma(-v_i, Q, A3[q]));
+            if constexpr (vol_pressure_sums<N>()) {
+                // P Sx = p_i (h_q Sx) at node i and p_q (-h_i Sx) at node q:
+                // the sums of h Sx, h Sy are scaled by the node's p = 2g h
+                // once per line (B2, B3), one product per pair fewer
+                const double h_q = sH[nq];
+                A2[i] = fma(sU[nq], Q, A2[i]);
+                A2[q] = fma(-u_i, Q, A2[q]);
+                A3[i] = fma(sV[nq], Q, A3[i]);
+                A3[q] = fma(-v_i, Q, A3[q]);
+                B2[i] = fma(h_q, c.x, B2[i]);
+                B2[q] = fma(-h_i, c.x, B2[q]);
+                B3[i] = fma(h_q, c.y, B3[i]);
+                B3[q] = fma(-h_i, c.y, B3[q]);
+            } else {
+                const double P = p_i * sH[nq];
+                A2[i] = fma(P, c.x, fma(sU[nq], Q, A2[i]));
+                A2[q] = fma(-P, c.x, fma(-u_i, Q, A2[q]));
+                A3[i] = fma(P, c.y, fma(sV[nq], Q, A3[i]));
+                A3[q] = fma(-P, c.y, fma(-v_i, Q, A3[q]));
+            }
         }
     }
 }
@@ -174,13 +201,23 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     const long long side = (valid ? k : 0) * 4 * n;
     const double ek = (AV && valid) ? a.eps[k] : 0.0;
     const bool visc = ek > 0.0;
-    double A1[n], A2[n], A3[n];
+    double A1[n], A2[n], A3[n], B2[n], B3[n];
 
     // ---- xi-line j = l ----------------------------------------------------
 #pragma unroll
-    for (int p = 0; p < n; ++p) A1[p] = A2[p] = A3[p] = 0.0;
+    for (int p = 0; p < n; ++p) A1[p] = A2[p] = A3[p] = B2[p] = B3[p] = 0.0;
     if (valid) {
-        pair_loop<N, BLK>(sm, e * nn + l * n, 1, pmx, A1, A2, A3);
+        pair_loop<N, BLK>(sm, e * nn + l * n, 1, pmx, A1, A2, A3, B2, B3);
+        if constexpr (vol_pressure_sums<N>()) {
+            // the pressure parts P Sx = 2g h_i h_q Sx: the node's 2g h times its sums
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                const double pp = S(F_P)[e * nn + l * n + p];
+                A2[p] = fma(pp, B2[p], A2[p]);
+                A3[p] = fma(pp, B3[p], A3[p]);
+                B2[p] = B3[p] = 0.0;
+            }
+        }
         // Lifts at the row's end nodes i = N (side 1) and i = 0 (side 3),
         // weighted by the tangential LGL weight w_l: done here, where every
         // lane holds one of them, rather than in the column phase where only
@@ -227,7 +264,17 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         A2[p] = S(F_A2)[e * nn + p * n + l];
         A3[p] = S(F_A3)[e * nn + p * n + l];
     }
-    if (valid) pair_loop<N, BLK>(sm, e * nn + l, n, pme, A1, A2, A3);
+    if (valid) {
+        pair_loop<N, BLK>(sm, e * nn + l, n, pme, A1, A2, A3, B2, B3);
+        if constexpr (vol_pressure_sums<N>()) {
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                const double pp = S(F_P)[e * nn + p * n + l];
+                A2[p] = fma(pp, B2[p], A2[p]);
+                A3[p] = fma(pp, B3[p], A3[p]);
+            }
+        }
+    }
     // own-velocity parts of the momentum fluxes, then the mass flux 2 sum Q
     // (before the viscous staging reuses the velocity planes)
 #pragma unroll
