@@ -167,6 +167,11 @@ int swe_status(swe_ctx* ctx, int* bits, void* stream);
  * milliseconds and the launch count since swe_timing(ctx, 1) (synchronises).
  * swe_launches returns the number of kernels the context launched so far. */
 int swe_timing(swe_ctx* ctx, int on);
+/* As swe_timing, for the kernel classes of `mask` only (bit c = class c;
+ * 0 turns timing off): the launches of the other classes get no events, so
+ * a timed loop that needs one class's launch time carries no event overhead
+ * for the rest. */
+int swe_timing_classes(swe_ctx* ctx, unsigned mask);
 int swe_timing_read(swe_ctx* ctx, int which, double* ms, int64_t* launches);
 int64_t swe_launches(const swe_ctx* ctx);
 

@@ -91,7 +91,7 @@ int set_last_error(int code, const std::string& msg) { return fail(code, msg); }
 
 Timed::Timed(swe_ctx* c_, int cls, cudaStream_t s_) : c(c_), s(s_) {
     c->launches++;
-    if (c->timing && c->ev_used < (int)c->ev_class.size()) {
+    if (c->timing && ((c->timing_mask >> cls) & 1u) && c->ev_used < (int)c->ev_class.size()) {
         idx = c->ev_used++;
         c->ev_class[idx] = cls;
         cudaEventRecord(c->ev[2 * idx], s);
@@ -947,7 +947,16 @@ extern "C" int swe_timing(swe_ctx* c, int on) {
         }
     }
     c->timing = on != 0;
+    c->timing_mask = ~0u;
     c->ev_used = 0;
+    return SWE_OK;
+}
+
+extern "C" int swe_timing_classes(swe_ctx* c, unsigned mask) {
+    if (!c) return fail(SWE_ERR_ARG, "swe_timing_classes: NULL context");
+    const int rc = swe_timing(c, mask != 0u);
+    if (rc) return rc;
+    c->timing_mask = mask;
     return SWE_OK;
 }
 

@@ -182,8 +182,9 @@ struct swe_ctx {
     // launch shapes (swe_autotune): volume threads per block, update warps per block
     int vol_tpb = 128;
     int upd_wpb = 4;
-    // timing
+    // timing: on, and the kernel classes whose launches get events (bit c = class c)
     bool timing = false;
+    unsigned timing_mask = ~0u;
     std::vector<cudaEvent_t> ev;
     std::vector<int> ev_class;
     int ev_used = 0;

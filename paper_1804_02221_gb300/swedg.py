@@ -20,7 +20,8 @@ KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "u
                   "reduce": 7, "adjoint": 8}
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
-           "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_read",
+           "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_classes",
+           "swe_timing_read",
            "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals",
            "swe_ens_create", "swe_ens_destroy", "swe_ens_size", "swe_ens_layout", "swe_ens_rhs",
            "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches", "swe_autotune",
@@ -78,6 +79,7 @@ def lib():
     L.swe_get_epsilon.argtypes = [vp, vp, vp]
     L.swe_status.argtypes = [vp, ctypes.POINTER(ctypes.c_int), vp]
     L.swe_timing.argtypes = [vp, ctypes.c_int]
+    L.swe_timing_classes.argtypes = [vp, ctypes.c_uint]
     L.swe_timing_read.argtypes = [vp, ctypes.c_int, dp, ctypes.POINTER(ctypes.c_int64)]
     L.swe_launches.argtypes = [vp]
     L.swe_launches.restype = ctypes.c_int64
@@ -242,8 +244,16 @@ class SweContext:
         _check(lib().swe_status(self._h, ctypes.byref(b), _stream(stream)))
         return b.value
 
-    def timing(self, on=True):
-        _check(lib().swe_timing(self._h, int(on)))
+    def timing(self, on=True, classes=None):
+        """Events around the context's launches: every kernel class, or only
+        the named ones (`classes`, names of KERNEL_CLASSES)."""
+        if classes is None:
+            _check(lib().swe_timing(self._h, int(on)))
+            return
+        mask = 0
+        for name in classes:
+            mask |= 1 << KERNEL_CLASSES[name]
+        _check(lib().swe_timing_classes(self._h, ctypes.c_uint(mask if on else 0)))
 
     def timing_read(self, which):
         ms, cnt = ctypes.c_double(), ctypes.c_int64()

@@ -85,3 +85,32 @@ def test_ensemble_autotune_then_step_matches_untuned():
     a.step(Wa, 0.0, 3)
     b.step(Wb, 0.0, 5)
     assert torch.equal(Wa, Wb)
+
+
+def test_timing_of_selected_kernel_classes():
+    """swe_timing brackets every launch with events; swe_timing_classes only
+    the launches of the chosen classes (the launch counter counts all)."""
+    swedg = swe_mod()
+    p = I.dam_break(N=3, K1=16)
+    c = swedg.SweContext.from_problem(p, **KW)
+    W = dev(p.W)
+    R0 = c.rhs(W)
+    c.timing(True)
+    c.rhs(W)
+    torch.cuda.synchronize()
+    for name in ("volume", "face", "av"):
+        ms, n = c.timing_read(name)
+        assert n == 1 and ms > 0.0, name
+    c.timing(True, classes=("volume",))
+    l0 = c.launches()
+    assert torch.equal(c.rhs(W), R0)
+    c.step(W, 0.0, 2)  # adaptive steps (CFL 0.5)
+    torch.cuda.synchronize()
+    ms, n = c.timing_read("volume")
+    assert n == 2 * 5 + 1 and ms > 0.0
+    for name in ("face", "av", "update", "prim"):
+        assert c.timing_read(name)[1] == 0, name
+    assert c.launches() - l0 > n
+    c.timing(False)
+    c.rhs(W)
+    assert c.timing_read("volume")[1] == 0
