@@ -138,6 +138,14 @@ int swe_mass(swe_ctx* ctx, const double* W, double* out3, void* stream);
 int swe_entropy(swe_ctx* ctx, const double* W, double* E, void* stream);
 /* Both in one pass: out4 = (mass, x momentum, y momentum, entropy), host. */
 int swe_integrals(swe_ctx* ctx, const double* W, double* out4, void* stream);
+/* swe_step (nsteps >= 1) followed by swe_integrals of the new state, with one
+ * synchronisation of `stream` and one device-to-host copy for the integrals,
+ * the step size and the status (swe_step and swe_integrals synchronise once
+ * each). On success W and out4 are bitwise what swe_step and swe_integrals
+ * give; on a failed step W is restored as by swe_step and out4 is left
+ * untouched. */
+int swe_step_integrals(swe_ctx* ctx, double* W, double dt, int nsteps, double* dt_last, double* out4,
+                       void* stream);
 
 /* Discrete entropy rate of device state W (Sec. 2: the entropy variables
  * q = (g(h+b) - (u^2+v^2)/2, u, v) of Eq. entropyVariables contracted with

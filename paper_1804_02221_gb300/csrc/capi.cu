@@ -378,7 +378,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     dst = dev_alloc(c, count, e2);                    \
     if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
     AL(W.uv, 2 * KN) AL(W.Fout, 3 * KS) AL(W.Ustar, 2 * KS) AL(W.eps, K) AL(W.Kreg, 3 * KN)
-    AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 4 * 608 + 8) AL(W.dt, 3 * (size_t)m.ninst + 1)
+    AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 4 * RED_BLOCKS + 8) AL(W.dt, 3 * (size_t)m.ninst + 1)
     if (p->av) {
         AL(W.Fvt, 4 * KN) AL(W.Fvtr, 4 * KS) AL(W.Fvout, 2 * KS)
     }
@@ -525,6 +525,37 @@ extern "C" int swe_step(swe_ctx* c, double* W, double dt, int nsteps, double* dt
         if (status & 2) return fail(SWE_ERR_NONFINITE, "swe_step: non-finite state; rolled back the failing step");
         return fail(SWE_ERR_NEG_MEAN, "swe_step: negative element mean water height; rolled back the failing step");
     }
+    return SWE_OK;
+}
+
+extern "C" int swe_step_integrals(swe_ctx* c, double* W, double dt, int nsteps, double* dt_last, double* out4,
+                                  void* stream) {
+    if (!c || !W || !out4 || nsteps < 1) return fail(SWE_ERR_ARG, "swe_step_integrals: bad argument");
+    if (!(dt > 0.0) && !(c->p.cfl > 0.0)) return fail(SWE_ERR_ARG, "swe_step_integrals: dt <= 0 needs cfl > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int* stop = c->w.status;
+    cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+    swe::launch_prim(c, W, s, stop);
+    for (int st = 0; st < nsteps; ++st) swe::step_once(c, W, dt, s, stop);
+    swe::launch_reduce_dev(c, W, 2, true, s);
+    int rc = check_launch("swe_step_integrals");
+    if (rc) return rc;
+    // integrals, step size and status in one copy
+    double h[6];
+    cudaMemcpyAsync(h, c->w.part + 4 * swe::RED_BLOCKS, 6 * sizeof(double), cudaMemcpyDeviceToHost, s);
+    cudaError_t e = cudaStreamSynchronize(s);
+    if (e != cudaSuccess) return cuda_fail(e, "swe_step_integrals");
+    const int status = (int)h[5];
+    if (status) {
+        cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+        cudaMemcpyAsync(W, c->w.Wn, 3 * c->m.KN * sizeof(double), cudaMemcpyDeviceToDevice, s);
+        e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_fail(e, "swe_step_integrals: rollback");
+        if (status & 2) return fail(SWE_ERR_NONFINITE, "swe_step_integrals: non-finite state; rolled back the failing step");
+        return fail(SWE_ERR_NEG_MEAN, "swe_step_integrals: negative element mean water height; rolled back the failing step");
+    }
+    for (int i = 0; i < 4; ++i) out4[i] = h[i];
+    if (dt_last) *dt_last = dt > 0.0 ? dt : h[4];
     return SWE_OK;
 }
 

@@ -520,7 +520,6 @@ __global__ void k_copy(long long count, const double* __restrict__ src, double* 
 // sums, then one warp per component adds the partials in a fixed order: the
 // result does not depend on scheduling.
 // ---------------------------------------------------------------------------
-constexpr int RED_BLOCKS = 608;
 constexpr int RED_THREADS = 256;
 
 __global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int what,
@@ -592,12 +591,19 @@ __global__ void k_rate_part(DeviceMesh m, const double* __restrict__ W, const do
 }
 
 // One warp per component: lane sums of a fixed stride, then a fixed butterfly.
-__global__ void k_reduce_final(const double* __restrict__ part, double* __restrict__ out) {
+// With status (nullable) also out[4] = dt[0], out[5] = the status word, so
+// that a step's results come back in one device-to-host copy.
+__global__ void k_reduce_final(const double* __restrict__ part, double* __restrict__ out,
+                               const double* __restrict__ dt = nullptr, const int* __restrict__ status = nullptr) {
     const int c = threadIdx.x >> 5, lane = threadIdx.x & 31;
     double s = 0.0;
     for (int b = lane; b < RED_BLOCKS; b += 32) s += part[c * RED_BLOCKS + b];
     s = warp_sum(s);
     if (lane == 0) out[c] = s;
+    if (threadIdx.x == 0 && status) {
+        out[4] = dt[0];
+        out[5] = (double)*(volatile const int*)status;
+    }
 }
 
 // Per-instance integrals of an ensemble group: block i sums the nodes of
@@ -718,15 +724,20 @@ void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cu
 }
 
 void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cudaStream_t s) {
+    launch_reduce_dev(c, W, what, false, s);
+    cudaMemcpyAsync(host_out, c->w.part + 4 * RED_BLOCKS, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
+}
+
+void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStream_t s) {
     {
         Timed tm(c, KC_REDUCE, s);
         k_reduce_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->m, W, what, c->w.part);
     }
-    {
-        Timed tm(c, KC_REDUCE, s);
+    Timed tm(c, KC_REDUCE, s);
+    if (pack)
+        k_reduce_final<<<1, 128, 0, s>>>(c->w.part, c->w.part + 4 * RED_BLOCKS, c->w.dt, c->w.status);
+    else
         k_reduce_final<<<1, 128, 0, s>>>(c->w.part, c->w.part + 4 * RED_BLOCKS);
-    }
-    cudaMemcpyAsync(host_out, c->w.part + 4 * RED_BLOCKS, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
 void launch_rate(swe_ctx* c, const double* W, const double* R, double* host_out, cudaStream_t s) {

@@ -13,6 +13,9 @@ namespace swe {
 
 constexpr int NMAX = SWE_NMAX;
 constexpr int NFACE = 4;
+// Blocks of the fixed-grid reductions; the work buffer `part` holds their
+// partials [4][RED_BLOCKS] followed by the results.
+constexpr int RED_BLOCKS = 608;
 
 // Basis of degree N on LGL nodes (Sec. 2.2) and the inverse Vandermonde
 // matrix of the normalised Legendre polynomials (App. A), row-major n x n.
@@ -133,7 +136,7 @@ struct Work {
     double* Kreg;   // [3][KN] 2N-storage register
     double* Wn;     // [3][KN] state at the start of a step
     double* R;      // [3][KN] right-hand side of the current stage
-    double* part;   // reduction partials
+    double* part;   // reduction partials [4][RED_BLOCKS], then the results (4 + dt + status)
     double* dt;     // [3][ninst]: dt in use, dt_cfl, dt_pos of every instance
     unsigned long long* dtbits;  // [ninst][2]: max of lambda/J, max of inverse positivity dt
     int* status;    // [1] status bits (shared by the groups of an ensemble)
@@ -234,7 +237,12 @@ void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double d
 void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, const int* stop);
 void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
                  const int* stop);
+// sum J w w W (what = 0), sum J w w e(W) (what = 1) or all four (what = 2)
+// into host_out[4] (asynchronous copy).
 void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cudaStream_t s);
+// The same into the device results w.part[4 * RED_BLOCKS + c]; pack: also
+// the step size in use (+4) and the status word (+5).
+void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStream_t s);
 // Per-instance (mass, momenta, entropy) of an ensemble group into device
 // out[4 * ninst]; ebeg (device, ninst + 1) holds the element ranges.
 void launch_reduce_inst(swe_ctx* c, const double* W, const long long* ebeg, double* out, cudaStream_t s);

@@ -21,7 +21,7 @@ KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "u
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_classes",
-           "swe_timing_read",
+           "swe_timing_read", "swe_step_integrals",
            "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals",
            "swe_ens_create", "swe_ens_destroy", "swe_ens_size", "swe_ens_layout", "swe_ens_rhs",
            "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches", "swe_autotune",
@@ -73,6 +73,7 @@ def lib():
     L.swe_limit.argtypes = [vp, vp, vp]
     L.swe_max_dt.argtypes = [vp, vp, dp, dp, vp]
     L.swe_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, dp, vp]
+    L.swe_step_integrals.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, dp, dp, vp]
     L.swe_mass.argtypes = [vp, vp, dp, vp]
     L.swe_entropy.argtypes = [vp, vp, dp, vp]
     L.swe_integrals.argtypes = [vp, vp, dp, vp]
@@ -210,6 +211,15 @@ class SweContext:
         if raise_on_error:
             _check(rc)
         return rc, dl.value
+
+    def step_integrals(self, W, dt=0.0, nsteps=1, stream=None):
+        """step, then (mass, x momentum, y momentum, entropy) of the new
+        state, with one synchronisation; returns (integrals, dt_last)."""
+        dl = ctypes.c_double(0.0)
+        out = (ctypes.c_double * 4)()
+        _check(lib().swe_step_integrals(self._h, self._state(W), float(dt), int(nsteps), ctypes.byref(dl), out,
+                                        _stream(stream)))
+        return np.array(out[:]), dl.value
 
     def mass(self, W, stream=None):
         out = (ctypes.c_double * 3)()

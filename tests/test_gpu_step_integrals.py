@@ -1,0 +1,84 @@
+"""swe_step_integrals: the step and the new state's integrals with one
+synchronisation. W and the integrals are bitwise those of swe_step followed
+by swe_integrals, for every launch shape; a failed step restores W and
+leaves the integrals alone."""
+import numpy as np
+import pytest
+
+from oracle import oracle as O
+from paper_1804_02221_gb300 import inputs as I
+
+torch = pytest.importorskip("torch")
+pytestmark = [pytest.mark.gpu,
+              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+
+AV = dict(eps0=0.03, sigma_min=-6.0, sigma_max=-0.5)
+
+
+def swe_mod():
+    from paper_1804_02221_gb300 import swedg
+    return swedg
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+@pytest.mark.parametrize("N,K1,rk,fixed,nsteps", [(1, 9, 0, False, 1), (3, 7, 1, False, 3), (5, 4, 0, True, 2),
+                                                   (7, 3, 0, False, 1), (12, 2, 1, True, 2)])
+def test_equals_step_then_integrals(N, K1, rk, fixed, nsteps):
+    swedg = swe_mod()
+    p = I.random_rough(N=N, K1=K1, seed=90 + N, dry_fraction=0.05)
+    kw = dict(flux=1, av=True, limiter=True, rk=rk, cfl=0.4, **AV)
+    c = swedg.SweContext.from_problem(p, **kw)
+    W0, _ = O.Oracle(p, **kw).limit(p.W)
+    # a fixed step: half the admissible one of the initial state
+    dt = 0.5 * min(c.max_dt(dev(W0))) if fixed else 0.0
+    Wa = dev(W0)
+    _, dta = c.step(Wa, dt, nsteps)
+    ref = c.integrals(Wa)
+    for vol, upd in ((128, 4), (64, 2), (128, 8)):
+        c.set_tuning(vol, upd)
+        Wb = dev(W0)
+        got, dtb = c.step_integrals(Wb, dt, nsteps)
+        assert torch.equal(Wa, Wb), (vol, upd)
+        assert np.array_equal(got, ref), (vol, upd)
+        assert dtb == dta
+    assert np.all(np.isfinite(ref)) and ref[0] > 0
+
+
+def test_failed_step_restores_state_and_bad_arguments():
+    swedg = swe_mod()
+    p = I.random_rough(N=3, K1=4, seed=9, dry_fraction=0.5)
+    kw = dict(flux=1, limiter=True, rk=1)
+    c = swedg.SweContext.from_problem(p, **kw)
+    W0, _ = O.Oracle(p, **kw).limit(p.W)
+    W = dev(W0)
+    with pytest.raises(swedg.SweError) as e:
+        c.step_integrals(W, 1e-3, 0)
+    assert e.value.code == swedg.ERR_ARG
+    with pytest.raises(swedg.SweError) as e:
+        c.step_integrals(W, 5.0, 1)   # far above the admissible step size
+    assert e.value.code in (swedg.ERR_NEG_MEAN, swedg.ERR_NONFINITE)
+    assert np.array_equal(W.cpu().numpy(), W0)
+    # the context is usable afterwards
+    dt = min(c.max_dt(W))
+    got, _ = c.step_integrals(W, dt, 1)
+    assert np.array_equal(got, c.integrals(W))
+
+
+def test_integrals_against_oracle_after_steps():
+    """Mass conservation and the oracle's integrals of the GPU state."""
+    swedg = swe_mod()
+    p = I.dam_break(N=4, K1=12)
+    kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    c = swedg.SweContext.from_problem(p, **kw)
+    W = dev(p.W)
+    m0 = c.integrals(W)
+    got, _ = c.step_integrals(W, 0.0, 5)
+    o = O.Oracle(p, **kw)
+    Wh = W.cpu().numpy()
+    mo, eo = o.mass(Wh), o.entropy(Wh)
+    assert np.abs(got[:3] - mo).max() < 1e-13 * np.abs(mo).max()
+    assert abs(got[3] - eo) < 1e-13 * abs(eo)
+    assert abs(got[0] - m0[0]) < 1e-12 * m0[0]
