@@ -146,6 +146,18 @@ int swe_integrals(swe_ctx* ctx, const double* W, double* out4, void* stream);
  * untouched. */
 int swe_step_integrals(swe_ctx* ctx, double* W, double dt, int nsteps, double* dt_last, double* out4,
                        void* stream);
+/* swe_step_integrals without any host synchronisation: enqueues the nsteps
+ * steps and the integrals of the resulting state on `stream` and returns.
+ * out6 (device, 6 doubles, owned by the caller) receives (mass, x momentum,
+ * y momentum, entropy, step size of the last step, status bits as a
+ * double). A failed step (status bit 1: negative element mean, bit 2:
+ * non-finite value) stops the call's remaining kernels and a device-side
+ * copy restores W to the start of the failing step, as swe_step does; the
+ * integrals are then those of the restored state, and the status stays set
+ * for swe_status until the next step call. Only argument errors and launch
+ * errors are returned here. Makes no host synchronisation and no
+ * allocation, so a CUDA graph may capture it (with timing off). */
+int swe_step_async(swe_ctx* ctx, double* W, double dt, int nsteps, double* out6, void* stream);
 
 /* Discrete entropy rate of device state W (Sec. 2: the entropy variables
  * q = (g(h+b) - (u^2+v^2)/2, u, v) of Eq. entropyVariables contracted with

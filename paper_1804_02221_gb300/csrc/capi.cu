@@ -559,6 +559,19 @@ extern "C" int swe_step_integrals(swe_ctx* c, double* W, double dt, int nsteps, 
     return SWE_OK;
 }
 
+extern "C" int swe_step_async(swe_ctx* c, double* W, double dt, int nsteps, double* out6, void* stream) {
+    if (!c || !W || !out6 || nsteps < 1) return fail(SWE_ERR_ARG, "swe_step_async: bad argument");
+    if (!(dt > 0.0) && !(c->p.cfl > 0.0)) return fail(SWE_ERR_ARG, "swe_step_async: dt <= 0 needs cfl > 0");
+    cudaStream_t s = (cudaStream_t)stream;
+    const int* stop = c->w.status;
+    cudaMemsetAsync(c->w.status, 0, sizeof(int), s);
+    swe::launch_prim(c, W, s, stop);
+    for (int st = 0; st < nsteps; ++st) swe::step_once(c, W, dt, s, stop);
+    swe::launch_restore(c, W, s);
+    swe::launch_reduce_dev(c, W, 2, true, s, out6);
+    return check_launch("swe_step_async");
+}
+
 // ---------------------------------------------------------------------------
 // Launch-shape tuning
 // ---------------------------------------------------------------------------

@@ -514,6 +514,16 @@ __global__ void k_copy(long long count, const double* __restrict__ src, double* 
         dst[i] = src[i];
 }
 
+// Device-side rollback of an asynchronous step: where the status word is set,
+// dst gets back src (the state at the start of the failing step).
+__global__ void k_restore(long long count, const double* __restrict__ src, double* __restrict__ dst,
+                          const int* status) {
+    if (*(volatile const int*)status == 0) return;
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = src[i];
+}
+
 // ---------------------------------------------------------------------------
 // Diagnostics: sum J w w W (what = 0, three sums), sum J w w e(W) (what = 1,
 // Eq. entropyFunction), or all four (what = 2). Fixed grid, per-block tree
@@ -728,16 +738,24 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
     cudaMemcpyAsync(host_out, c->w.part + 4 * RED_BLOCKS, 4 * sizeof(double), cudaMemcpyDeviceToHost, s);
 }
 
-void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStream_t s) {
+void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStream_t s, double* dst) {
     {
         Timed tm(c, KC_REDUCE, s);
         k_reduce_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->m, W, what, c->w.part);
     }
     Timed tm(c, KC_REDUCE, s);
+    double* out = dst ? dst : c->w.part + 4 * RED_BLOCKS;
     if (pack)
-        k_reduce_final<<<1, 128, 0, s>>>(c->w.part, c->w.part + 4 * RED_BLOCKS, c->w.dt, c->w.status);
+        k_reduce_final<<<1, 128, 0, s>>>(c->w.part, out, c->w.dt, c->w.status);
     else
-        k_reduce_final<<<1, 128, 0, s>>>(c->w.part, c->w.part + 4 * RED_BLOCKS);
+        k_reduce_final<<<1, 128, 0, s>>>(c->w.part, out);
+}
+
+void launch_restore(swe_ctx* c, double* W, cudaStream_t s) {
+    const long long count = 3 * c->m.KN;
+    Timed tm(c, KC_UPDATE, s);
+    k_restore<<<grid_for(count, 256) > 4096 ? 4096 : grid_for(count, 256), 256, 0, s>>>(count, c->w.Wn, W,
+                                                                                         c->w.status);
 }
 
 void launch_rate(swe_ctx* c, const double* W, const double* R, double* host_out, cudaStream_t s) {

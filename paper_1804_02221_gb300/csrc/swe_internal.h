@@ -240,9 +240,13 @@ void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cu
 // sum J w w W (what = 0), sum J w w e(W) (what = 1) or all four (what = 2)
 // into host_out[4] (asynchronous copy).
 void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cudaStream_t s);
-// The same into the device results w.part[4 * RED_BLOCKS + c]; pack: also
-// the step size in use (+4) and the status word (+5).
-void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStream_t s);
+// The same into the device results w.part[4 * RED_BLOCKS + c] (or dst[c],
+// when given); pack: also the step size in use (+4) and the status word (+5).
+void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStream_t s,
+                       double* dst = nullptr);
+// W = the state saved at the start of the step (w.Wn) where the status word
+// is set: the rollback of a failed step without a host synchronisation.
+void launch_restore(swe_ctx* c, double* W, cudaStream_t s);
 // Per-instance (mass, momenta, entropy) of an ensemble group into device
 // out[4 * ninst]; ebeg (device, ninst + 1) holds the element ranges.
 void launch_reduce_inst(swe_ctx* c, const double* W, const long long* ebeg, double* out, cudaStream_t s);

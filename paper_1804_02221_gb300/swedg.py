@@ -21,7 +21,7 @@ KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "u
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_classes",
-           "swe_timing_read", "swe_step_integrals",
+           "swe_timing_read", "swe_step_integrals", "swe_step_async",
            "swe_launches", "swe_info", "swe_last_error", "swe_integrals_noalloc", "swe_integrals",
            "swe_ens_create", "swe_ens_destroy", "swe_ens_size", "swe_ens_layout", "swe_ens_rhs",
            "swe_ens_max_dt", "swe_ens_step", "swe_ens_integrals", "swe_ens_launches", "swe_autotune",
@@ -74,6 +74,7 @@ def lib():
     L.swe_max_dt.argtypes = [vp, vp, dp, dp, vp]
     L.swe_step.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, dp, vp]
     L.swe_step_integrals.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, dp, dp, vp]
+    L.swe_step_async.argtypes = [vp, vp, ctypes.c_double, ctypes.c_int, vp, vp]
     L.swe_mass.argtypes = [vp, vp, dp, vp]
     L.swe_entropy.argtypes = [vp, vp, dp, vp]
     L.swe_integrals.argtypes = [vp, vp, dp, vp]
@@ -220,6 +221,19 @@ class SweContext:
         _check(lib().swe_step_integrals(self._h, self._state(W), float(dt), int(nsteps), ctypes.byref(dl), out,
                                         _stream(stream)))
         return np.array(out[:]), dl.value
+
+    def step_async(self, W, dt=0.0, nsteps=1, out=None, stream=None):
+        """step and integrals enqueued without a host synchronisation; `out`
+        (device, 6 doubles, allocated here unless given) receives (mass, x
+        momentum, y momentum, entropy, last step size, status bits)."""
+        import torch
+        if out is None:
+            out = torch.empty(6, dtype=torch.float64, device=W.device)
+        if out.dtype != torch.float64 or not out.is_cuda or not out.is_contiguous() or out.numel() < 6:
+            raise ValueError("out must be a contiguous CUDA float64 tensor of 6 elements")
+        _check(lib().swe_step_async(self._h, self._state(W), float(dt), int(nsteps), ctypes.c_void_p(out.data_ptr()),
+                                    _stream(stream)))
+        return out
 
     def mass(self, W, stream=None):
         out = (ctypes.c_double * 3)()

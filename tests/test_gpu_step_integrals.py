@@ -82,3 +82,72 @@ def test_integrals_against_oracle_after_steps():
     assert np.abs(got[:3] - mo).max() < 1e-13 * np.abs(mo).max()
     assert abs(got[3] - eo) < 1e-13 * abs(eo)
     assert abs(got[0] - m0[0]) < 1e-12 * m0[0]
+
+
+def test_async_step_equals_synchronous_step():
+    swedg = swe_mod()
+    p = I.random_rough(N=4, K1=6, seed=31, dry_fraction=0.1)
+    kw = dict(flux=1, av=True, limiter=True, rk=0, cfl=0.4, **AV)
+    c = swedg.SweContext.from_problem(p, **kw)
+    W0, _ = O.Oracle(p, **kw).limit(p.W)
+    Wa = dev(W0)
+    ints, dta = c.step_integrals(Wa, 0.0, 2)
+    Wb = dev(W0)
+    out = c.step_async(Wb, 0.0, 2)
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert torch.equal(Wa, Wb)
+    assert np.array_equal(o[:4], ints) and o[4] == dta and o[5] == 0.0
+
+
+def test_async_failed_step_rolls_back_on_the_device():
+    swedg = swe_mod()
+    p = I.random_rough(N=3, K1=4, seed=9, dry_fraction=0.5)
+    kw = dict(flux=1, limiter=True, rk=1)
+    c = swedg.SweContext.from_problem(p, **kw)
+    W0, _ = O.Oracle(p, **kw).limit(p.W)
+    W = dev(W0)
+    out = c.step_async(W, 5.0, 1)   # far above the admissible step size
+    torch.cuda.synchronize()
+    o = out.cpu().numpy()
+    assert int(o[5]) & 3
+    assert np.array_equal(W.cpu().numpy(), W0)
+    assert np.array_equal(o[:4], c.integrals(W))
+    assert c.status() & 3
+    with pytest.raises(swedg.SweError) as e:
+        c.step_async(W, 1e-3, 0)
+    assert e.value.code == swedg.ERR_ARG
+    dt = min(c.max_dt(W))
+    o2 = c.step_async(W, dt, 1).cpu().numpy()
+    assert o2[5] == 0.0
+
+
+def test_async_step_replays_in_a_cuda_graph():
+    """Captured once, replayed three times: the same bits as three
+    swe_step calls (adaptive step sizes computed on the device)."""
+    swedg = swe_mod()
+    p = I.dam_break(N=3, K1=12)
+    kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    c = swedg.SweContext.from_problem(p, **kw)
+    Wr = dev(p.W)
+    for _ in range(3):
+        c.step(Wr, 0.0, 1)
+    ref = c.integrals(Wr)
+    W = dev(p.W)
+    W0 = dev(p.W)
+    out = torch.zeros(6, dtype=torch.float64, device="cuda")
+    c.step_async(W, 0.0, 1, out)      # warm-up outside the capture
+    torch.cuda.synchronize()
+    W.copy_(W0)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        c.step_async(W, 0.0, 1, out)
+    W.copy_(W0)                       # capture does not run the work
+    torch.cuda.synchronize()
+    for _ in range(3):
+        g.replay()
+    torch.cuda.synchronize()
+    assert torch.equal(W, Wr)
+    o = out.cpu().numpy()
+    assert np.array_equal(o[:4], ref) and o[5] == 0.0
