@@ -38,10 +38,10 @@
  *    source).
  *
  * Pins: every function is checked by the CPU tests against closed forms,
- * identities or brute force, except one sub-case: the solid-wall term of
- * the positivity time step in orc_max_dt (mirror state at a wall face) is
- * parity unpinned (a wall carries no mass flux, so positivity cannot
- * observe it; it is exercised only by GPU parity).
+ * identities or brute force. The solid-wall term of the positivity time
+ * step in orc_max_dt (mirror state at a wall face) is pinned by its closed
+ * form w0 (J/|n|)/(2c) on an element closed by walls (Lemma PosPres with
+ * {u~} = 0 and B = 0 there).
  */
 #include "orc.h"
 

@@ -11,6 +11,8 @@ an interior face), and the BR1 wall treatment adds no boundary term to the
 viscous entropy identity of Thm. 1. The dry dam break of Sec. 6.1.1 keeps
 mass to round-off and its entropy decreasing, as the paper reports.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -160,6 +162,36 @@ def test_wall_time_step_uses_the_mirror_state():
     o = O.Oracle(p, flux=1, limiter=True)
     dc, dp = o.max_dt(p.W)
     assert np.isfinite(dc) and np.isfinite(dp) and dp > 0
+
+
+@pytest.mark.parametrize("N", [1, 3, 6])
+def test_wall_time_step_closed_form(N):
+    """The wall term of Lemma PosPres with the mirror state, by hand: at a
+    wall node h+ = h-, u~+ = -u~-, so {u~} = 0, {c} = c, A = 2c and B = 0;
+    the jump term needs B [[u~]] < 0 and drops out, and the node's bound is
+    w0 (J/|n|) / (2c) with w0 = 2/(N(N+1)) and |n| the length of the
+    unscaled outward normal, whatever the velocity. One curved element closed
+    by walls on all four sides has dt_pos = the minimum of that over its side
+    nodes (geometry from the test's own metric terms). The box is stretched
+    to 0.8 x 2.6 so that |n| differs from 1 and between the faces."""
+    p = I.random_walls(N=N, Kx=1, Ky=1, seed=20 + N, walls=(True, True))
+    p = dataclasses.replace(p, x=0.4 * p.x, y=1.3 * p.y)
+    assert (np.asarray(p.EToE) < 0).all()
+    o = O.Oracle(p, flux=1, limiter=True)
+    _, dtp = o.max_dt(p.W)
+    geo = refmath.geometry(p.x, p.y, N)
+    c = np.sqrt(p.g * np.maximum(p.W[0], 0.0))
+    w0 = 2.0 / (N * (N + 1))
+    want = np.inf
+    for f in range(4):
+        nx, ny = refmath.outward_normal(geo, f)
+        t = w0 * refmath.face_slice(geo[4], f) / np.hypot(nx, ny) / (2.0 * refmath.face_slice(c, f))
+        want = min(want, float(t.min()))
+    assert abs(dtp - want) <= 1e-13 * want
+    # the velocities do not enter the wall term
+    W2 = p.W.copy()
+    W2[1:] *= -3.7
+    assert o.max_dt(W2)[1] == dtp
 
 
 def test_dry_dam_break_mass_and_entropy():
