@@ -42,6 +42,8 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--N", type=int, default=7)
     ap.add_argument("--K1", type=int, default=None)
+    ap.add_argument("--rhs-reps", type=int, default=1000,
+                    help="right-hand sides per RHS-alone rate (mean and median of one call)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
@@ -273,6 +275,28 @@ def rhs_rate(ctx, W0, R, nodes, reps=10):
     return nodes / (a.elapsed_time(b) / reps * 1e-3)
 
 
+def rhs_stats(ctx, W0, R, nodes, reps):
+    """`reps` right-hand sides back to back after two untimed ones, an event
+    between consecutive calls: node-updates/s from the mean time, and the
+    mean and median time of one call (the paper's protocol: the mean of
+    1000 evaluations)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    for _ in range(2):
+        ctx.rhs(W0, R)
+    torch.cuda.synchronize()
+    ev = [torch.cuda.Event(enable_timing=True) for _ in range(reps + 1)]
+    ev[0].record(stream)
+    for i in range(reps):
+        ctx.rhs(W0, R)
+        ev[i + 1].record(stream)
+    torch.cuda.synchronize()
+    t = sorted(ev[i].elapsed_time(ev[i + 1]) for i in range(reps))
+    mean = ev[0].elapsed_time(ev[reps]) / reps
+    med = t[reps // 2] if reps % 2 else 0.5 * (t[reps // 2 - 1] + t[reps // 2])
+    return {"node_updates_per_s": nodes / (mean * 1e-3), "ms_mean": mean, "ms_median": med, "reps": reps}
+
+
 def split_vs_standard(prob, W0, R):
     """The paper's GPU comparison (Eq. VolInt): the split-form volume kernel
     against the standard one on the same state (ES interface flux, no AV, so
@@ -323,19 +347,13 @@ def sweep(args):
         ms = e0.elapsed_time(e1) / args.steps
         vol_ms, vol_n = ctx.timing_read("volume")
         ctx.timing(False)
-        rates = {}
+        rates, med = {}, {}
         R = torch.empty_like(W0)
         for name, kk in (("ES+AV", kw), ("EC", dict(flux=0))):
             c2 = ctx if name == "ES+AV" else swedg.SweContext.from_problem(prob, **kk)
-            for _ in range(2):
-                c2.rhs(W0, R)
-            a, bb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            a.record(stream)
-            for _ in range(10):
-                c2.rhs(W0, R)
-            bb.record(stream)
-            torch.cuda.synchronize()
-            rates[name] = prob.nodes / (a.elapsed_time(bb) / 10 * 1e-3)
+            st = rhs_stats(c2, W0, R, prob.nodes, args.rhs_reps)
+            rates[name] = st["node_updates_per_s"]
+            med[name] = st["ms_median"]
             if c2 is not ctx:
                 c2.close()
         vol = vol_ms / vol_n
@@ -344,7 +362,8 @@ def sweep(args):
         cmp = split_vs_standard(prob, W0, R)
         print(json.dumps({"sweep": True, "N": N, "K": prob.K, "nodes": prob.nodes, "ms_per_step": ms,
                           "node_updates_per_s": RK_STAGES * prob.nodes / (ms * 1e-3),
-                          "rhs_node_updates_per_s": rates, "volume_ms": vol,
+                          "rhs_node_updates_per_s": rates, "rhs_ms_median": med, "rhs_reps": args.rhs_reps,
+                          "volume_ms": vol,
                           "volume_tflops": achieved, "volume_frac_at_2070MHz": achieved / peak,
                           "volume_gbs_algorithmic": volume_bytes_per_node(N) * prob.nodes / (vol * 1e-3) / 1e9,
                           "split_vs_standard": cmp}), flush=True)
@@ -685,20 +704,13 @@ def main():
     check_steps(res_h)
 
     # ---- RHS alone: entropy-conservative vs entropy-stable + AV ----
-    rhs_rates = {}
+    rhs_rates, rhs_median = {}, {}
     R = torch.empty_like(W0)
     for name, kk in (("ES+AV", kw), ("EC", dict(flux=0))):
         c2 = ctx if name == "ES+AV" else swedg.SweContext.from_problem(prob, **kk)
-        for _ in range(3):
-            c2.rhs(W0, R)
-        torch.cuda.synchronize()
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        a.record(stream)
-        for _ in range(10):
-            c2.rhs(W0, R)
-        b.record(stream)
-        torch.cuda.synchronize()
-        rhs_rates[name] = nodes / (a.elapsed_time(b) / 10 * 1e-3)
+        st = rhs_stats(c2, W0, R, nodes, args.rhs_reps)
+        rhs_rates[name] = st["node_updates_per_s"]
+        rhs_median[name] = st["ms_median"]
 
     # ---- the paper's comparison: split-form vs standard volume kernel ----
     cmp = None if args.no_compare else split_vs_standard(prob, W0, R)
@@ -743,6 +755,7 @@ def main():
         "kernels_note": "per-class event times from a pass of its own (every launch bracketed by events); "
                         "the timed steps carry events around the volume kernel only",
         "rhs_only_node_updates_per_s": rhs_rates,
+        "rhs_only_ms_median": rhs_median, "rhs_only_reps": args.rhs_reps,
         "launch_shapes": {"volume_threads_per_block": shapes[0], "update_warps_per_block": shapes[1]},
         "split_vs_standard": cmp,
         "scalar_updates_per_s": 3 * value,
