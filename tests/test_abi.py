@@ -95,6 +95,9 @@ def test_null_contexts_are_rejected():
     lib = swedg.lib()
     assert lib.swe_rhs(None, None, None, None) == swedg.ERR_ARG
     assert lib.swe_step(None, None, 0.0, 1, None, None) == swedg.ERR_ARG
+    assert lib.swe_step_integrals(None, None, 0.0, 1, None, None, None) == swedg.ERR_ARG
+    assert lib.swe_step_async(None, None, 0.0, 1, None, None) == swedg.ERR_ARG
+    assert lib.swe_timing_classes(None, 1) == swedg.ERR_ARG
     assert lib.swe_rhs_adjoint(None, None, None, None, None, None) == swedg.ERR_ARG
     assert lib.swe_gauge_misfit(None, None, 0, None, None, None, None, None, None, None) == swedg.ERR_ARG
     lib.swe_destroy(None)
