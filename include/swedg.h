@@ -71,7 +71,19 @@ typedef struct swe_ctx swe_ctx;
  *            1 the standard volume term of Eq. VolInt (second line), D applied
  *            to the nodal contravariant fluxes, with the non-split source
  *            -g h J grad b (the paper's comparison scheme: neither entropy
- *            stable nor well balanced). */
+ *            stable nor well balanced).
+ * cfl_visc:  0 keeps the paper's time-step rule. > 0 (with av) adds the
+ *            viscous restriction of the AV term, which the paper does not
+ *            have: a node of an element with viscosity eps_k (of the state
+ *            at the start of the step) adds the rate eps_k kv a^2 to
+ *            lambda/J, a = (|a_xi| + |a_eta|)/J, kv = (N+1)^3 cfl /
+ *            (8 cfl_visc); alone it limits dt to
+ *            16 cfl_visc / (eps_k a^2 (N+1)^4), i.e. cfl_visc dx^2 /
+ *            (eps_k (N+1)^4) on an affine square element of side dx. With a
+ *            fixed eps0 the explicit AV term otherwise becomes unstable as
+ *            the mesh is refined (0.25 keeps the 4.2M-node dam break of
+ *            the benchmark stable). Appended last: callers that zero the
+ *            struct get the paper's rule. */
 typedef struct {
     int flux;
     int av;
@@ -83,6 +95,7 @@ typedef struct {
     int rk;
     double cfl;
     int volume;
+    double cfl_visc;
 } swe_params;
 
 /* Build a context (Sec. 2.1: curvilinear map, metric terms, Jacobian

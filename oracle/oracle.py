@@ -40,7 +40,7 @@ class Params(ctypes.Structure):
     _fields_ = [("flux", ctypes.c_int), ("av", ctypes.c_int), ("eps0", ctypes.c_double),
                 ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
                 ("limiter", ctypes.c_int), ("h_tol", ctypes.c_double), ("rk", ctypes.c_int),
-                ("cfl", ctypes.c_double), ("volume", ctypes.c_int)]
+                ("cfl", ctypes.c_double), ("volume", ctypes.c_int), ("cfl_visc", ctypes.c_double)]
 
 
 _lib = None
@@ -131,11 +131,11 @@ class Oracle:
     """Oracle instance for one Problem (see paper_1804_02221_gb300.inputs)."""
 
     def __init__(self, prob, flux=1, av=False, eps0=0.0, sigma_min=math.nan, sigma_max=math.nan,
-                 limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0):
+                 limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0, cfl_visc=0.0):
         self.prob = prob
         self.N, self.K, self.n = prob.N, prob.K, prob.N + 1
         self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
-                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume))
+                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume), float(cfl_visc))
         self._x = np.ascontiguousarray(prob.x, dtype=np.float64)
         self._y = np.ascontiguousarray(prob.y, dtype=np.float64)
         self._b = np.ascontiguousarray(prob.b, dtype=np.float64)

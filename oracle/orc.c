@@ -37,6 +37,10 @@
  *    J b_y = -x_eta b_xi + x_xi b_eta (the continuous limit of the split
  *    source).
  *
+ * Time step: orc_max_dt follows the paper's rule (CFL and positivity); with
+ * cfl_visc > 0 it adds a viscous restriction of the AV term that the paper
+ * does not have (see orc_max_dt).
+ *
  * Pins: every function is checked by the CPU tests against closed forms,
  * identities or brute force. The solid-wall term of the positivity time
  * step in orc_max_dt (mirror state at a wall face) is pinned by its closed
@@ -317,6 +321,7 @@ int orc_create(int N, int K, const double* x, const double* y, const int* EToE,
     if (!out || !x || !y || !EToE || !EToF || !flip || !b || !p) return ORC_ERR_ARG;
     *out = NULL;
     if (N < 1 || N > ORC_NMAX || K < 1 || !(g > 0.0)) return ORC_ERR_ARG;
+    if (!(p->cfl_visc >= 0.0) || isinf(p->cfl_visc)) return ORC_ERR_ARG;
     orc_mesh* m = (orc_mesh*)calloc(1, sizeof(orc_mesh));
     m->N = N;
     m->n = N + 1;
@@ -911,19 +916,33 @@ int orc_max_dt(orc_mesh* m, const double* W, double* dt_cfl, double* dt_pos) {
     size_t nn = (size_t)K * n * n;
     double g = m->g;
     double min_ratio = INFINITY; /* min over nodes of J / (lambda_xi + lambda_eta) */
+    /* Optional viscous restriction of the AV term (cfl_visc > 0; not in the
+     * paper, whose rule has none): a node whose element has viscosity eps_k
+     * (App. A, of the state W itself) adds the rate J eps_k kv a^2 with
+     * a = (|a_xi| + |a_eta|)/J and kv = (N+1)^3 CFL / (8 cfl_visc), so that
+     * this term alone gives dt = 16 cfl_visc / (eps_k a^2 (N+1)^4), i.e.
+     * cfl_visc dx^2 / (eps_k (N+1)^4) on an affine square element of side dx. */
+    double kv = (m->p.av && m->p.cfl_visc > 0.0) ? pow(N + 1.0, 3) * m->p.cfl / (8.0 * m->p.cfl_visc) : 0.0;
+    double* epsk = kv > 0.0 ? dalloc((size_t)K) : NULL;
+    for (int k = 0; kv > 0.0 && k < K; ++k) epsk[k] = element_epsilon(m, W, k);
     for (size_t id = 0; id < nn; ++id) {
         double h = W[id], u = velocity(h, W[nn + id]), v = velocity(h, W[2 * nn + id]);
         double c = sqrt(g * fmax(h, 0.0));
-        double lxi = fabs(m->y_eta[id] * u - m->x_eta[id] * v)
-                   + c * sqrt(m->y_eta[id] * m->y_eta[id] + m->x_eta[id] * m->x_eta[id]);
-        double leta = fabs(-m->y_xi[id] * u + m->x_xi[id] * v)
-                    + c * sqrt(m->y_xi[id] * m->y_xi[id] + m->x_xi[id] * m->x_xi[id]);
+        double axi = sqrt(m->y_eta[id] * m->y_eta[id] + m->x_eta[id] * m->x_eta[id]);
+        double aeta = sqrt(m->y_xi[id] * m->y_xi[id] + m->x_xi[id] * m->x_xi[id]);
+        double lxi = fabs(m->y_eta[id] * u - m->x_eta[id] * v) + c * axi;
+        double leta = fabs(-m->y_xi[id] * u + m->x_xi[id] * v) + c * aeta;
         double lam = lxi + leta;
+        if (kv > 0.0) {
+            double a = (axi + aeta) / m->J[id];
+            lam += m->J[id] * epsk[id / ((size_t)n * n)] * kv * a * a;
+        }
         if (lam > 0.0) {
             double t = m->J[id] / lam;
             if (t < min_ratio) min_ratio = t;
         }
     }
+    free(epsk);
     double cfl = m->p.cfl * 2.0 / (N + 1.0) * min_ratio;
     double pos = INFINITY;
     double w0 = 2.0 / (N * (N + 1.0));

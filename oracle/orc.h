@@ -48,6 +48,8 @@ typedef struct {
     int volume;       /* 0: split-form volume term (Eq. fluxDiffFormF with Eq. Fmij),
                          1: standard volume term (Eq. VolInt, second line) with the
                          non-split source -g h J grad b (reading in orc.c) */
+    double cfl_visc;  /* 0: the paper's time-step rule; > 0 (with av): also the viscous
+                         restriction of the AV term (not in the paper; see orc_max_dt) */
 } orc_params;
 
 typedef struct orc_mesh orc_mesh;

@@ -128,6 +128,8 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     if (p->volume != 0 && p->volume != 1) return fail(SWE_ERR_ARG, "swe_create: volume must be 0 or 1");
     if (p->av && !(p->eps0 >= 0.0)) return fail(SWE_ERR_ARG, "swe_create: eps0 must be >= 0");
     if (!isnan(p->h_tol) && !(p->h_tol >= 0.0)) return fail(SWE_ERR_ARG, "swe_create: h_tol must be >= 0");
+    if (!(p->cfl_visc >= 0.0) || isinf(p->cfl_visc))
+        return fail(SWE_ERR_ARG, "swe_create: cfl_visc must be finite and >= 0");
     const int n = N + 1, nn = n * n;
     const long long KN = (long long)K * nn, KS = (long long)K * 4 * n;
     if (KN * 3 > 2147483647LL) return fail(SWE_ERR_ARG, "swe_create: mesh too large for 32-bit node ids");
@@ -335,6 +337,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     c->sigma_min = isnan(p->sigma_min) ? s0 - 1.0 : p->sigma_min;
     c->sigma_max = isnan(p->sigma_max) ? s0 + 1.0 : p->sigma_max;
     c->h_tol = isnan(p->h_tol) ? 1e-4 : p->h_tol;
+    c->kv = (p->av && p->cfl_visc > 0.0) ? pow(N + 1.0, 3) * p->cfl / (8.0 * p->cfl_visc) : 0.0;
     DeviceMesh& m = c->m;
     m.N = N;
     m.n = n;
@@ -442,12 +445,23 @@ void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int
 void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop, bool save) {
     const bool adaptive = !(dt > 0.0);
     const double* dtd = adaptive ? c->w.dt : nullptr;
+    // the viscous restriction needs eps of the step's start state: the time
+    // step then runs after the first stage's AV kernel (which computes it)
+    const bool visc_dt = adaptive && c->kv > 0.0;
     if (save) launch_copy(c, W, c->w.Wn, 3 * c->m.KN, s, stop);
-    if (adaptive) launch_dt(c, W, 0.0, s, stop);
+    if (adaptive && !visc_dt) launch_dt(c, W, 0.0, s, stop);
     const int stages = c->p.rk == 0 ? 5 : 3;
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int stage = 0; stage < stages; ++stage) {
-        rhs_chain(c, W, c->w.R, s, stop, true);
+        if (stage == 0 && visc_dt) {
+            launch_surface(c, W, s, stop);
+            launch_av(c, W, s, stop, false);
+            launch_dt(c, W, 0.0, s, stop);
+            launch_visc_face(c, s, stop);
+            launch_volume(c, W, c->w.R, s, stop);
+        } else {
+            rhs_chain(c, W, c->w.R, s, stop, true);
+        }
         if (c->p.rk == 0)
             launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop, true);
         else
@@ -486,6 +500,10 @@ extern "C" int swe_max_dt(swe_ctx* c, const double* W, double* dt_cfl, double* d
     if (!c || !W) return fail(SWE_ERR_ARG, "swe_max_dt: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     swe::launch_prim(c, W, s, nullptr);
+    if (c->kv > 0.0) {  // the element viscosities of W for the viscous restriction
+        swe::launch_surface(c, W, s, nullptr);
+        swe::launch_av(c, W, s, nullptr, false);
+    }
     swe::launch_dt(c, W, 0.0, s, nullptr);
     double h[4];
     cudaMemcpyAsync(h, c->w.dt, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -406,6 +406,8 @@ struct DtArgs {
     const double* cfl_n;
     int pos;
     unsigned long long* bits;
+    const double* eps;  // element viscosities of W (read when kv > 0)
+    double kv;          // viscous restriction factor; 0: the paper's rule
     const int* stop;
 };
 
@@ -430,13 +432,18 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, bool va
     const DeviceMesh& m = a.m;
     const double g = m.g;
     unsigned long long lamb = 0;
+    // viscous restriction (kv > 0, uniform): the node's rate gains eps_k kv a^2
+    const double ekv = (a.kv > 0.0 && valid) ? a.eps[k] * a.kv : 0.0;
     for (int node = sub; node < nn && valid; node += G) {
         const long long id = k * nn + node;
         const double h = a.W[id], u = a.uv[id], v = a.uv[m.KN + id];
         const double c = sqrt_pos(g * pos_part(h));
         sc[node] = c;
         const double vel = fabs(fma(m.axx[id], u, m.axy[id] * v)) + fabs(fma(m.aex[id], u, m.aey[id] * v));
-        lamb = max_bits(lamb, fma(c, a.cfl_n[id], m.rJ[id] * vel));
+        const double an = a.cfl_n[id];
+        double lam = fma(c, an, m.rJ[id] * vel);
+        if (a.kv > 0.0) lam = fma(ekv * an, an, lam);
+        lamb = max_bits(lamb, lam);
     }
     const double lam = seg_max<G>(__longlong_as_double((long long)lamb));
     unsigned long long* bits = a.bits + 2 * (valid && m.inst ? m.inst[k] : 0);
@@ -718,7 +725,7 @@ void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double d
 
 void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, const int* stop) {
     cudaMemsetAsync(c->w.dtbits, 0, 2 * sizeof(unsigned long long) * c->m.ninst, s);
-    DtArgs a{c->m, W, c->w.uv, c->m.nax, (c->p.limiter && c->p.flux) ? 1 : 0, c->w.dtbits, stop};
+    DtArgs a{c->m, W, c->w.uv, c->m.nax, (c->p.limiter && c->p.flux) ? 1 : 0, c->w.dtbits, c->w.eps, c->kv, stop};
 #define SWE_DT(NN) dt_n<NN>(c, a, s)
     SWE_SWITCH_N(c->m.N, SWE_DT)
 #undef SWE_DT

@@ -185,6 +185,8 @@ struct swe_ctx {
     // launch shapes (swe_autotune): volume threads per block, update warps per block
     int vol_tpb = 128;
     int upd_wpb = 4;
+    // viscous time-step factor kv = (N+1)^3 cfl / (8 cfl_visc); 0 = the paper's rule
+    double kv = 0.0;
     // timing: on, and the kernel classes whose launches get events (bit c = class c)
     bool timing = false;
     unsigned timing_mask = ~0u;

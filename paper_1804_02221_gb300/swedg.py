@@ -34,7 +34,7 @@ class Params(ctypes.Structure):
     _fields_ = [("flux", ctypes.c_int), ("av", ctypes.c_int), ("eps0", ctypes.c_double),
                 ("sigma_min", ctypes.c_double), ("sigma_max", ctypes.c_double),
                 ("limiter", ctypes.c_int), ("h_tol", ctypes.c_double), ("rk", ctypes.c_int),
-                ("cfl", ctypes.c_double), ("volume", ctypes.c_int)]
+                ("cfl", ctypes.c_double), ("volume", ctypes.c_int), ("cfl_visc", ctypes.c_double)]
 
 
 class Instance(ctypes.Structure):
@@ -153,14 +153,15 @@ class SweContext:
     """One mesh + parameter set on the current CUDA device (swe_create)."""
 
     def __init__(self, N, K, x, y, EToE, EToF, flip, b, g=9.81, flux=1, av=False, eps0=0.0,
-                 sigma_min=math.nan, sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0):
+                 sigma_min=math.nan, sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0,
+                 cfl_visc=0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("swedg needs a CUDA device; there is no CPU path")
         L = lib()
         self.N, self.K, self.n = int(N), int(K), int(N) + 1
         self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
-                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume))
+                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume), float(cfl_visc))
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, b)]
         cons = [np.ascontiguousarray(a, dtype=np.int32) for a in (EToE, EToF, flip)]
         d = lambda a: a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
@@ -364,13 +365,13 @@ class SweEnsemble:
     `view(W, i)` is instance i's (3, K, n, n) view into it."""
 
     def __init__(self, problems, g=9.81, flux=1, av=False, eps0=0.0, sigma_min=math.nan,
-                 sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0):
+                 sigma_max=math.nan, limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0, cfl_visc=0.0):
         import torch
         if not torch.cuda.is_available():
             raise RuntimeError("swedg needs a CUDA device; there is no CPU path")
         L = lib()
         self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
-                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume))
+                             int(limiter), float(h_tol), int(rk), float(cfl), int(volume), float(cfl_visc))
         self.ninst = len(problems)
         keep = []
         arr = (Instance * self.ninst)()

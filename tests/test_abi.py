@@ -75,7 +75,8 @@ def test_create_rejects_bad_parameters():
            swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 2, 0.5, 0),   # rk
            swedg.Params(1, 1, -1.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 0),  # eps0
            swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, -1.0, 0, 0.5, 0),           # h_tol
-           swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 3)]   # volume
+           swedg.Params(1, 0, 0.0, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 3),   # volume
+           swedg.Params(1, 1, 0.1, float("nan"), float("nan"), 0, float("nan"), 0, 0.5, 0, -1.0)]  # cfl_visc
     for p in bad:
         rc, _ = _call_create(3, 1, p)
         assert rc == swedg.ERR_ARG

@@ -402,3 +402,74 @@ def test_time_order(rk, order):
         errs.append(np.abs(W - ref).max())
     rate = math.log(errs[-2] / errs[-1], 2)
     assert rate > order - 0.3, (errs, rate)
+
+
+# ---------------------------------------------------------------------------
+# Optional viscous restriction of the time step (cfl_visc > 0; not in the
+# paper, whose rule has none)
+# ---------------------------------------------------------------------------
+
+def _cartesian_rough(N, K1, dx_total=2.0, seed=4):
+    zero = lambda X, Y: (0.0 * X, 0.0 * Y)
+    x, y, xw, yw, E, F, fl = I.periodic_mesh(N, K1, K1, (0.0, dx_total, 0.0, dx_total), zero)
+    rng = np.random.default_rng(seed)
+    h = 1.0 + 0.3 * rng.uniform(-1, 1, size=x.shape)
+    z = np.zeros_like(h)
+    return I.Problem("cartesian_rough", N, K1, K1, x, y, z, np.stack([h, z, z]), E, F, fl, 9.81)
+
+
+@pytest.mark.parametrize("N,K1", [(2, 3), (5, 4), (7, 2)])
+def test_viscous_time_step_closed_form(N, K1):
+    """Affine square elements of side dx, a rough height at rest, every
+    element at the full viscosity eps0 (sigma_max far below the element's
+    smoothness measure): each node's rate is c a + eps0 kv a^2 with
+    a = (|a_xi| + |a_eta|)/J = 4/dx and kv = (N+1)^3 CFL/(8 cfl_visc), so
+    dt_cfl = CFL 2/(N+1) / (c_max 4/dx + eps0 kv 16/dx^2); with cfl_visc = 0
+    or without AV the paper's rule c_max 4/dx alone."""
+    p = _cartesian_rough(N, K1)
+    dx = 2.0 / K1
+    cmax = np.sqrt(p.g * p.W[0].max())
+    cfl, eps0, cv = 0.5, 0.04, 0.3
+    base = dict(flux=1, av=True, eps0=eps0, sigma_min=-31.0, sigma_max=-30.0, cfl=cfl)
+    kv = (N + 1) ** 3 * cfl / (8.0 * cv)
+    got = O.Oracle(p, cfl_visc=cv, **base).max_dt(p.W)[0]
+    want = cfl * 2.0 / (N + 1) / (cmax * 4.0 / dx + eps0 * kv * 16.0 / dx ** 2)
+    assert abs(got - want) <= 1e-13 * want
+    paper = cfl * 2.0 / (N + 1) / (cmax * 4.0 / dx)
+    assert abs(O.Oracle(p, **base).max_dt(p.W)[0] - paper) <= 1e-13 * paper
+    assert O.Oracle(p, cfl_visc=cv, **dict(base, av=False)).max_dt(p.W)[0] == O.Oracle(p, **base).max_dt(p.W)[0]
+
+
+def test_viscous_time_step_scales_with_dx_squared_over_eps():
+    """Dominated by the viscous term (small cfl_visc), the step falls with the
+    square of the element size and inversely with eps0."""
+    cfl, cv = 0.5, 1e-4
+    def dt(K1, eps0):
+        p = _cartesian_rough(3, K1)
+        kw = dict(flux=1, av=True, eps0=eps0, sigma_min=-31.0, sigma_max=-30.0, cfl=cfl, cfl_visc=cv)
+        return O.Oracle(p, **kw).max_dt(p.W)[0]
+    r_dx = dt(2, 0.05) / dt(4, 0.05)
+    r_eps = dt(2, 0.05) / dt(2, 0.1)
+    assert abs(r_dx - 4.0) < 0.01 and abs(r_eps - 2.0) < 0.005
+
+
+def test_viscous_time_step_keeps_the_dam_break_stable():
+    """The main workload's dam break at N = 7 on 64 x 64 quads with
+    eps0 = 0.025: under the paper's rule the explicit AV term outgrows the
+    step (|W| > 10 within 50 steps, or a failed step); with cfl_visc = 0.25
+    the same 50 steps keep |W| bounded and the entropy falling in every
+    step."""
+    p = I.dam_break(N=7, K1=64)
+    kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    o = O.Oracle(p, **kw)
+    W, rc, _ = o.step(p.W, 0.0, 50)
+    assert rc != 0 or np.abs(W).max() > 10.0
+    o = O.Oracle(p, cfl_visc=0.25, **kw)
+    W = p.W.copy()
+    E = [o.entropy(W)]
+    for _ in range(50):
+        W, rc, _ = o.step(W, 0.0, 1)
+        assert rc == 0
+        E.append(o.entropy(W))
+    assert np.abs(W).max() < 3.0
+    assert np.all(np.diff(E) <= 1e-13 * abs(E[0])) and E[-1] < E[0]
