@@ -426,14 +426,14 @@ constexpr int DT_WPB = 4;  // warps (elements) per block of the time-step kernel
 // shared memory (sc, the group's n*n slots) for the own side of the
 // positivity part. The maxima of non-negative values and the sign tests are
 // integer operations on the bit patterns.
-template <int N, int G>
+template <int N, int G, bool VISC>
 __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, bool valid, int sub, double* sc) {
     constexpr int n = N + 1, nn = n * n;
     const DeviceMesh& m = a.m;
     const double g = m.g;
     unsigned long long lamb = 0;
-    // viscous restriction (kv > 0, uniform): the node's rate gains eps_k kv a^2
-    const double ekv = (a.kv > 0.0 && valid) ? a.eps[k] * a.kv : 0.0;
+    // viscous restriction (VISC, kv > 0): the node's rate gains eps_k kv a^2
+    const double ekv = (VISC && valid) ? a.eps[k] * a.kv : 0.0;
     for (int node = sub; node < nn && valid; node += G) {
         const long long id = k * nn + node;
         const double h = a.W[id], u = a.uv[id], v = a.uv[m.KN + id];
@@ -442,7 +442,7 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, bool va
         const double vel = fabs(fma(m.axx[id], u, m.axy[id] * v)) + fabs(fma(m.aex[id], u, m.aey[id] * v));
         const double an = a.cfl_n[id];
         double lam = fma(c, an, m.rJ[id] * vel);
-        if (a.kv > 0.0) lam = fma(ekv * an, an, lam);
+        if (VISC) lam = fma(ekv * an, an, lam);
         lamb = max_bits(lamb, lam);
     }
     const double lam = seg_max<G>(__longlong_as_double((long long)lamb));
@@ -485,7 +485,7 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, bool va
     __syncwarp();  // the next element reuses sc
 }
 
-template <int N>
+template <int N, bool VISC>
 __global__ void __launch_bounds__(32 * DT_WPB) k_dt(DtArgs a) {
     constexpr int G = elem_lanes<N>(), EPW = 32 / G, nn = (N + 1) * (N + 1);
     __shared__ double sc[DT_WPB][EPW * nn];
@@ -494,7 +494,7 @@ __global__ void __launch_bounds__(32 * DT_WPB) k_dt(DtArgs a) {
     const int sub = lane & (G - 1), grp = lane / G;
     for (long long kb = ((long long)blockIdx.x * wpb + w) * EPW; kb < a.m.K; kb += (long long)gridDim.x * wpb * EPW) {
         const long long k = kb + grp;
-        dt_element<N, G>(a, k, k < a.m.K, sub, sc[w] + grp * nn);
+        dt_element<N, G, VISC>(a, k, k < a.m.K, sub, sc[w] + grp * nn);
     }
 }
 
@@ -667,7 +667,9 @@ void update_n(swe_ctx* c, int mode, const UpdArgs& a, cudaStream_t s) {
 template <int N>
 void dt_n(swe_ctx* c, const DtArgs& a, cudaStream_t s) {
     Timed tm(c, KC_DT, s);
-    k_dt<N><<<persistent_grid(c, DT_WPB * (32 / elem_lanes<N>())), 32 * DT_WPB, 0, s>>>(a);
+    const int grid = persistent_grid(c, DT_WPB * (32 / elem_lanes<N>()));
+    if (a.kv > 0.0) k_dt<N, true><<<grid, 32 * DT_WPB, 0, s>>>(a);
+    else k_dt<N, false><<<grid, 32 * DT_WPB, 0, s>>>(a);
 }
 
 #define SWE_SWITCH_N(N, CALL)                                                         \
