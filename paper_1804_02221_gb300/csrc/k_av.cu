@@ -22,9 +22,9 @@
 //   E_top = S_yxi + S_yeta - (2k+1) B0^2
 //   E_sub = S_zxi - (k+1) B2^2 + S_zeta - (k+1) C0^2 - C2^2
 // which costs O(N^2) per element instead of the O(N^3) transform. One warp
-// evaluates 8 elements at a time (16 for N = 2, 3 and 32 for N = 1), so the
-// per-element reductions are short butterflies over 4 (2, 1) lanes and the
-// scalar work runs on 8 (16, 32) lanes at once.
+// evaluates 32 elements at a time up to N = 4 (16 for N = 5..8, 8 above), so
+// the per-element sums need no butterfly (1 lane; 2, 4 lanes) and the scalar
+// work runs on 32 (16, 8) lanes at once.
 #include <math.h>
 
 #include "kcommon.cuh"
@@ -46,12 +46,14 @@ struct AvArgs {
 
 constexpr int AV_WPB = 2;  // warps per block
 
-// Elements per warp: 8 from N = 4 up; more for the small elements of low
-// degree, where the per-element scalar work (the eight sums, epsilon) would
-// otherwise dominate (N = 1: 32, N = 2 and 3: 16).
+// Elements per warp: 32 up to N = 4, 16 for N = 5..8, 8 above (measured on
+// the dam break at 4.2M nodes: 32 instead of 16 at N = 2, 3 and of 8 at N = 4
+// took 12-17% off the kernel, 16 instead of 8 at N = 5 and 7 took 4-5%). More
+// elements per warp spread the per-element scalar work (the eight sums,
+// epsilon) over more lanes and keep more loads in flight.
 template <int N>
 constexpr int av_epw() {
-    return N == 1 ? 32 : (N <= 3 ? 16 : 8);
+    return N <= 4 ? 32 : (N <= 8 ? 16 : 8);
 }
 
 // epsilon from the nine sums of one element (S_yxi, S_yeta, S_zxi, S_zeta,
