@@ -22,9 +22,9 @@
 //   E_top = S_yxi + S_yeta - (2k+1) B0^2
 //   E_sub = S_zxi - (k+1) B2^2 + S_zeta - (k+1) C0^2 - C2^2
 // which costs O(N^2) per element instead of the O(N^3) transform. One warp
-// evaluates 32 elements at a time up to N = 4 (16 for N = 5..8, 8 above), so
-// the per-element sums need no butterfly (1 lane; 2, 4 lanes) and the scalar
-// work runs on 32 (16, 8) lanes at once.
+// evaluates several elements at a time (8 to 32, av_epw), so the per-element
+// sums are short butterflies over 32/av_epw lanes and the scalar work runs on
+// av_epw lanes at once.
 #include <math.h>
 
 #include "kcommon.cuh"
@@ -46,14 +46,18 @@ struct AvArgs {
 
 constexpr int AV_WPB = 2;  // warps per block
 
-// Elements per warp: 32 up to N = 4, 16 for N = 5..8, 8 above (measured on
-// the dam break at 4.2M nodes: 32 instead of 16 at N = 2, 3 and of 8 at N = 4
-// took 12-17% off the kernel, 16 instead of 8 at N = 5 and 7 took 4-5%). More
-// elements per warp spread the per-element scalar work (the eight sums,
-// epsilon) over more lanes and keep more loads in flight.
-template <int N>
+// Elements per warp. Wide: 32 up to N = 4, 16 for N = 5..8, 8 above
+// (measured on the dam break at 4.2M nodes: 32 instead of 16 at N = 2, 3 and
+// of 8 at N = 4 took 12-17% off the kernel, 16 instead of 8 at N = 5 and 7
+// took 4-5%): more elements per warp spread the per-element scalar work (the
+// eight sums, epsilon) over more lanes and keep more loads in flight. Narrow:
+// 32 at N = 1, 16 at N = 2, 3, 8 above, for meshes too small to give the wide
+// mapping enough warps (64 x 64 quads at N = 4: 64 blocks for 152 SMs, the
+// kernel 1.8x slower than narrow).
+template <int N, bool WIDE>
 constexpr int av_epw() {
-    return N <= 4 ? 32 : (N <= 8 ? 16 : 8);
+    if (WIDE) return N <= 4 ? 32 : (N <= 8 ? 16 : 8);
+    return N == 1 ? 32 : (N <= 3 ? 16 : 8);
 }
 
 // epsilon from the nine sums of one element (S_yxi, S_yeta, S_zxi, S_zeta,
@@ -85,9 +89,9 @@ __device__ __forceinline__ double epsilon_from_sums(const double* S, const EpsPa
 
 // EPS_GIVEN: epsilon of this state is already in the work buffer; only the
 // viscous fluxes remain.
-template <int N, bool EPS_GIVEN>
+template <int N, bool EPS_GIVEN, bool WIDE>
 __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
-    constexpr int AV_EPW = av_epw<N>();
+    constexpr int AV_EPW = av_epw<N, WIDE>();
     constexpr int LPE = 32 / AV_EPW;  // lanes per element for the sums (4, 2 or 1)
     constexpr int SPL = 8 / LPE;      // projection sums per lane (2, 4 or 8)
     constexpr int n = N + 1, nn = n * n, P4 = 4 * n, PER = (nn + 31) / 32;
@@ -264,10 +268,17 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
 
 template <int N>
 void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s, bool eps_given) {
-    const int blocks = grid_for(c->m.K, AV_WPB * av_epw<N>());
+    // the wide mapping when it still gives at least 8 warps per SM
+    const bool wide = c->m.K >= (long long)av_epw<N, true>() * 8 * c->sms;
+    const int blocks = grid_for(c->m.K, AV_WPB * (wide ? av_epw<N, true>() : av_epw<N, false>()));
     Timed tm(c, KC_AV, s);
-    if (eps_given) k_av<N, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
-    else k_av<N, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+    if (wide) {
+        if (eps_given) k_av<N, true, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+        else k_av<N, false, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+    } else {
+        if (eps_given) k_av<N, true, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+        else k_av<N, false, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+    }
 }
 
 }  // namespace
