@@ -129,9 +129,13 @@ int swe_rhs(swe_ctx* ctx, const double* W, double* R, void* stream);
  * is and recorded in the status read by swe_status. */
 int swe_limit(swe_ctx* ctx, double* W, void* stream);
 
-/* Largest admissible time step for device state W: the CFL rule (dt_cfl) and
- * the positivity restrictions of Lemma PosPres, Eq. CFLConstraints (dt_pos,
- * +inf when limiter = 0 or flux = 0). Host outputs; synchronises `stream`. */
+/* Largest admissible time step for device state W: the CFL rule (dt_cfl,
+ * including the viscous restriction when cfl_visc > 0, for which the element
+ * viscosities of W are computed first) and the positivity restrictions of
+ * Lemma PosPres, Eq. CFLConstraints (dt_pos, +inf when limiter = 0 or
+ * flux = 0). Host outputs; synchronises `stream`; overwrites the context's
+ * scratch buffers (velocities, and with cfl_visc > 0 the interface and AV
+ * work buffers). */
 int swe_max_dt(swe_ctx* ctx, const double* W, double* dt_cfl, double* dt_pos, void* stream);
 
 /* Advance device state W in place by nsteps steps of the chosen Runge-Kutta
