@@ -287,12 +287,18 @@ int swe_info(const swe_ctx* ctx, int* N, int* K, int* nfaces);
  * afford the device synchronisation implied by cudaMalloc/cudaFree, and hosts
  * with a memory budget fixed at start-up. The call computes the same sums as
  * swe_mass and swe_entropy without a context:
- *   out4[0..2] = sum_k sum_ij wJ W_c,  out4[3] = sum_k sum_ij wJ e(W)
- * (e of Eq. entropyFunction), with
+ *   out4[0..2] = sum_k sum_ij wJ W_c,  out4[3] = sum_k sum_ij wJ e(W),
+ *   e = (hu^2 + hv^2)/(2h) + g h^2/2 + g h b  (kinetic part 0 where h <= 0),
+ * with
  *   W    device, 3*K*(N+1)^2 doubles, the state planes (h, hu, hv);
  *   wJ   device, K*(N+1)^2 doubles, w_i w_j J at every node;
  *   b    device, K*(N+1)^2 doubles, the bathymetry;
  *   out4 device, 4 doubles, written asynchronously on `stream`.
+ * All four must be device (or managed) memory of the current device, and
+ * `stream` must belong to it: a pointer of another device or of host memory
+ * is rejected with SWE_ERR_ARG before any launch. The sizes are the caller's
+ * promise: the kernels read exactly 3*K*(N+1)^2, K*(N+1)^2 and K*(N+1)^2
+ * doubles and write 4.
  * It allocates nothing: the per-element partial sums live in one fixed
  * device array of 4*SWE_NOALLOC_MAX_ELEMENTS doubles (2 MiB), which every GPU
  * that loads the library holds until the process exits. K above

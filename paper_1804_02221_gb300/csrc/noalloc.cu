@@ -73,6 +73,25 @@ __global__ void k_sum_integrals(int K, const double* __restrict__ partials, doub
 
 int nfail(const std::string& m) { return set_last_error(SWE_ERR_ARG, m); }
 
+// 0 if p is device (or managed) memory that the current device `dev` can
+// use directly; an error code (with the message set) otherwise. A pointer of
+// another device would make the kernels read across devices or fault.
+int check_pointer(const void* p, const char* name, int dev) {
+    cudaPointerAttributes a{};
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();  // the failed query sets the (non-sticky) last error: clear it
+        return nfail(std::string("swe_integrals_noalloc: ") + name + " is not a CUDA allocation");
+    }
+    if (a.type == cudaMemoryTypeManaged) return SWE_OK;
+    if (a.type != cudaMemoryTypeDevice)
+        return nfail(std::string("swe_integrals_noalloc: ") + name + " is not device memory");
+    if (a.device != dev)
+        return nfail(std::string("swe_integrals_noalloc: ") + name + " is on device " + std::to_string(a.device) +
+                     ", the current device is " + std::to_string(dev));
+    return SWE_OK;
+}
+
 }  // namespace
 }  // namespace swe
 
@@ -92,6 +111,14 @@ extern "C" int swe_integrals_noalloc(int N, int K, const double* W, const double
                                                 cudaGetErrorString(e));
     }
     if (dev < 0 || dev >= kMaxDevices) return nfail("swe_integrals_noalloc: device index out of range");
+    {
+        const void* ptrs[4] = {W, wJ, b, out4};
+        const char* names[4] = {"W", "wJ", "b", "out4"};
+        for (int i = 0; i < 4; ++i) {
+            int rc = check_pointer(ptrs[i], names[i], dev);
+            if (rc != SWE_OK) return rc;
+        }
+    }
     double* scratch = nullptr;
     {
         // First call on each device: resolve the device address of the

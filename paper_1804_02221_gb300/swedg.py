@@ -135,17 +135,38 @@ def _stream(stream):
 def integrals_noalloc(N, W, wJ, b, g, out4=None, stream=None):
     """swe_integrals_noalloc: mass, momenta and entropy of device state W
     without a context and without any allocation by the library (the output
-    tensor out4 is allocated here unless the caller passes one)."""
+    tensor out4 is allocated here unless the caller passes one).
+
+    W is (3, K, N+1, N+1); wJ and b hold K (N+1)^2 doubles each; all tensors
+    are contiguous float64 on one CUDA device, and the call runs with that
+    device current (on `stream`, which must belong to it, or on its current
+    stream). Shapes and devices are checked here before the library is
+    called, since the kernels trust the sizes they are given."""
     import torch
-    K = W.shape[1]
-    if out4 is None:
-        out4 = torch.empty(4, dtype=torch.float64, device=W.device)
-    for a in (W, wJ, b, out4):
+    N = int(N)
+    n = N + 1
+    if W.dim() != 4 or W.shape[0] != 3 or W.shape[2] != n or W.shape[3] != n:
+        raise ValueError(f"swe_integrals_noalloc: W must be (3, K, {n}, {n}), got {tuple(W.shape)}")
+    K = int(W.shape[1])
+    for name, a in (("wJ", wJ), ("b", b)):
+        if a.numel() != K * n * n:
+            raise ValueError(f"swe_integrals_noalloc: {name} holds {a.numel()} values, not K (N+1)^2 = {K * n * n}")
+    if out4 is not None and out4.numel() < 4:
+        raise ValueError("swe_integrals_noalloc: out4 must hold at least 4 values")
+    tensors = (W, wJ, b) + ((out4,) if out4 is not None else ())
+    for a in tensors:
         if not (a.is_cuda and a.dtype == torch.float64 and a.is_contiguous()):
             raise ValueError("swe_integrals_noalloc needs contiguous float64 CUDA tensors")
-    _check(lib().swe_integrals_noalloc(int(N), int(K), ctypes.c_void_p(W.data_ptr()),
-                                       ctypes.c_void_p(wJ.data_ptr()), ctypes.c_void_p(b.data_ptr()),
-                                       float(g), ctypes.c_void_p(out4.data_ptr()), _stream(stream)))
+    if len({a.device for a in tensors}) != 1:
+        raise ValueError("swe_integrals_noalloc: W, wJ, b and out4 must be on one CUDA device")
+    if stream is not None and getattr(stream, "device", W.device) != W.device:
+        raise ValueError("swe_integrals_noalloc: the stream belongs to another device")
+    with torch.cuda.device(W.device):
+        if out4 is None:
+            out4 = torch.empty(4, dtype=torch.float64, device=W.device)
+        _check(lib().swe_integrals_noalloc(N, K, ctypes.c_void_p(W.data_ptr()),
+                                           ctypes.c_void_p(wJ.data_ptr()), ctypes.c_void_p(b.data_ptr()),
+                                           float(g), ctypes.c_void_p(out4.data_ptr()), _stream(stream)))
     return out4
 
 

@@ -9,12 +9,27 @@ matrix alone is computed by another (equally exact) formula moves R by
 9e-12 relative to max|R| on the lake-plus-hump state. The scale is
   T = g max(h)^2 max_nodes (|a_xi| + |a_eta|)/J * N(N+1)/2,
 the largest single term of the flux difference (N(N+1)/2 = 1/omega_0 is the
-largest entry of D~), and the right-hand-side error is measured relative to
-max(|R|_inf, T).
+largest entry of D~).
+
+Every right-hand-side comparison reports two figures:
+  plain   = |Rg - Ro|_inf / |Ro|_inf           (the plain relative L-infinity)
+  scaled  = |Rg - Ro|_inf / max(|Ro|_inf, T)   (relative to the term scale)
+and asserts scaled <= RHS_TOL_T. Where the state is far from equilibrium
+(T/|R| small) the two agree; near equilibrium the plain figure grows with
+T/|R|. Each comparison is recorded in RECORDS; conftest prints the table at
+the end of the run (and writes it as JSON where PARITY_LOG names a file).
 """
+import os
+
 import numpy as np
 
 import refmath
+
+# measured GPU-oracle differences reach 1.2e-14 of T (N=12, 4.2M nodes);
+# the bar keeps a margin of ~4 above that
+RHS_TOL_T = 5e-14
+
+RECORDS = []
 
 
 def term_scale(prob, W=None):
@@ -24,9 +39,29 @@ def term_scale(prob, W=None):
     return prob.g * np.abs(W[0]).max() ** 2 * a.max() * prob.N * (prob.N + 1) / 2.0
 
 
+def rhs_errors(Rg, Ro, prob, W=None):
+    """(plain, scaled, T/|R|) for one right-hand side."""
+    d = float(np.abs(Rg - Ro).max())
+    r = float(np.abs(Ro).max())
+    T = float(term_scale(prob, W))
+    plain = d / r if r > 0 else (0.0 if d == 0 else float("inf"))
+    return plain, d / max(r, T), (T / r if r > 0 else float("inf"))
+
+
 def rhs_err(Rg, Ro, prob, W=None):
     """|Rg - Ro|_inf / max(|Ro|_inf, T)."""
-    return np.abs(Rg - Ro).max() / max(np.abs(Ro).max(), term_scale(prob, W))
+    return rhs_errors(Rg, Ro, prob, W)[1]
+
+
+def check_rhs(Rg, Ro, prob, W=None, tol=RHS_TOL_T, label=""):
+    """Record both figures and assert the term-scaled one."""
+    plain, scaled, ratio = rhs_errors(Rg, Ro, prob, W)
+    test = os.environ.get("PYTEST_CURRENT_TEST", "?").split(" ")[0]
+    RECORDS.append(dict(test=test, label=label, N=int(prob.N), K=int(prob.K), plain=plain,
+                        scaled=scaled, T_over_R=ratio))
+    assert np.isfinite(Rg).all(), f"{test} {label}: non-finite right-hand side"
+    assert scaled <= tol, f"{test} {label}: {scaled:.3e} of T > {tol:.0e} (plain {plain:.3e})"
+    return plain, scaled
 
 
 def rel(a, b):

@@ -4,6 +4,8 @@ import ctypes
 import os
 import re
 
+import pytest
+
 from paper_1804_02221_gb300 import build as B
 from paper_1804_02221_gb300 import swedg
 
@@ -103,3 +105,28 @@ def test_null_contexts_are_rejected():
     assert lib.swe_gauge_misfit(None, None, 0, None, None, None, None, None, None, None) == swedg.ERR_ARG
     lib.swe_destroy(None)
     lib.swe_ens_destroy(None)
+
+
+def test_noalloc_wrapper_checks_shapes_before_the_library(monkeypatch):
+    """integrals_noalloc refuses mis-shaped or host tensors before it calls
+    the library (its kernels trust the sizes they are given)."""
+    torch = pytest.importorskip("torch")
+
+    def no_library():
+        raise AssertionError("the library must not be called")
+    monkeypatch.setattr(swedg, "lib", no_library)
+    f64 = dict(dtype=torch.float64)
+    N, K = 3, 4
+    W, wJ, b = torch.zeros(3, K, 4, 4, **f64), torch.zeros(K, 4, 4, **f64), torch.zeros(K, 4, 4, **f64)
+    with pytest.raises(ValueError, match="W must be"):
+        swedg.integrals_noalloc(N, torch.zeros(3, K, 4, 5, **f64), wJ, b, 9.81)
+    with pytest.raises(ValueError, match="W must be"):
+        swedg.integrals_noalloc(N, torch.zeros(2, K, 4, 4, **f64), wJ, b, 9.81)
+    with pytest.raises(ValueError, match="wJ holds"):
+        swedg.integrals_noalloc(N, W, torch.zeros(K - 1, 4, 4, **f64), b, 9.81)
+    with pytest.raises(ValueError, match="b holds"):
+        swedg.integrals_noalloc(N, W, wJ, torch.zeros(K, 16, **f64)[:, :15], 9.81)
+    with pytest.raises(ValueError, match="out4"):
+        swedg.integrals_noalloc(N, W, wJ, b, 9.81, out4=torch.zeros(3, **f64))
+    with pytest.raises(ValueError, match="CUDA"):
+        swedg.integrals_noalloc(N, W, wJ, b, 9.81)

@@ -1,18 +1,20 @@
 """Parity of the CUDA library (through its C ABI) with the CPU oracle on the
 same seeded inputs.
 
-Tolerances: 1e-12 per right-hand side, relative to max(|R|_inf, T) with T the
+Tolerances: 5e-14 per right-hand side, relative to max(|R|_inf, T) with T the
 size of the largest term of the flux difference (see parity.py for why the
-cancelled result alone is not the right scale near equilibrium); 1e-10
-relative L-infinity of the state after 100 Runge-Kutta steps.
+cancelled result alone is not the right scale near equilibrium; the plain
+relative L-infinity is recorded beside it for every case); 1e-10 relative
+L-infinity of the state after 100 Runge-Kutta steps.
 """
 import math
+import os
 
 import numpy as np
 import pytest
 
 import refmath
-from parity import rel, rhs_err
+from parity import check_rhs, rel
 from oracle import oracle as O
 from paper_1804_02221_gb300 import inputs as I
 
@@ -20,8 +22,8 @@ torch = pytest.importorskip("torch")
 pytestmark = [pytest.mark.gpu,
               pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
 
-RHS_TOL = 1e-12
 STEP_TOL = 1e-10
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "lake_hump_exact_rhs.npz")
 
 
 def swe_mod():
@@ -61,7 +63,7 @@ def test_rhs_parity_inviscid(N, Kx, Ky, rot, flux):
         rng = np.random.default_rng(N)
         p.W = p.W * (1 + 0.05 * rng.uniform(-1, 1, size=p.W.shape))
     Ro, Rg, _, _ = rhs_both(p, flux=flux)
-    assert rhs_err(Rg, Ro, p) < RHS_TOL
+    check_rhs(Rg, Ro, p)
 
 
 @pytest.mark.parametrize("N,Kx,rot", [(1, 4, None), (2, 5, 1), (3, 8, 2), (4, 6, None), (5, 4, 3),
@@ -74,7 +76,7 @@ def test_rhs_parity_viscous(N, Kx, rot):
     eg = g.epsilon().cpu().numpy()
     assert eo.max() > 0 and np.all(eo < kw["eps0"]), "the case must exercise the sine ramp of App. A"
     assert np.abs(eg - eo).max() < 1e-12 * kw["eps0"]
-    assert rhs_err(Rg, Ro, p) < RHS_TOL
+    check_rhs(Rg, Ro, p)
 
 
 @pytest.mark.parametrize("N", [3, 5])
@@ -86,7 +88,38 @@ def test_rhs_parity_partially_viscous(N):
     eo = o.epsilon()
     assert 0 < np.count_nonzero(eo) < p.K
     assert np.abs(g.epsilon().cpu().numpy() - eo).max() < 1e-12
-    assert rhs_err(Rg, Ro, p) < RHS_TOL
+    check_rhs(Rg, Ro, p)
+
+
+def test_rhs_parity_lake_hump_configuration():
+    """The lake-plus-hump configuration (N=3, 8x8 curved periodic quads, ES
+    flux, AV, limiter), at t = 0 and after 50 oracle steps: a state near
+    equilibrium, where |R| is three orders of magnitude below the term scale."""
+    p = I.lake_hump(N=3, K1=8)
+    kw = dict(flux=1, av=True, eps0=0.01, limiter=True, rk=0, cfl=0.5)
+    o, g = pair(p, **kw)
+    check_rhs(g.rhs(dev(p.W)).cpu().numpy(), o.rhs(p.W), p, label="t=0")
+    W, rc, _ = o.step(p.W, 0.0, 50)
+    assert rc == 0
+    check_rhs(g.rhs(dev(W)).cpu().numpy(), o.rhs(W), p, W, label="50 steps")
+
+
+def test_rhs_lake_hump_against_exact():
+    """The GPU right-hand side against the exact (40-digit) right-hand side of
+    the same float64 inputs (tests/golden/lake_hump_exact_rhs.npz, written by
+    the multi-precision brute force): on this near-equilibrium state the FP64
+    oracle itself is ~2e-12 of |R| from the exact result, and the GPU must be
+    as close as the oracle is (both ~1e-15 of T)."""
+    d = np.load(GOLDEN)
+    p = I.lake_hump(N=3, K1=8)
+    p.x, p.y, p.b = d["x"], d["y"], d["b"]
+    kw = dict(flux=1, av=True, eps0=0.01, limiter=True)
+    o, g = pair(p, **kw)
+    for lab, W, R in (("exact t=0", d["W0"], d["R0"]), ("exact 50 st", d["W50"], d["R50"])):
+        Rg = g.rhs(dev(W)).cpu().numpy()
+        _, sg = check_rhs(Rg, R, p, W, label=lab)
+        _, so = check_rhs(o.rhs(W), R, p, W, label=lab + " orc")
+        assert sg <= 4 * so + 1e-15
 
 
 @pytest.mark.parametrize("N,rot", [(1, None), (3, 7), (4, 8), (7, 9), (12, None)])
@@ -187,7 +220,7 @@ def test_entropy_and_velocities_wide_range_of_heights():
     Ro = o.rhs(W)
     Rg = g.rhs(dev(W)).cpu().numpy()
     assert np.isfinite(Rg).all()
-    assert rhs_err(Rg, Ro, p, W) < RHS_TOL
+    check_rhs(Rg, Ro, p, W)
 
 
 def test_step_parity_lake_hump_100_lsrk():
@@ -215,7 +248,7 @@ def test_step_parity_thacker_ssp(N, rot):
     differences of whole elements: the oracle built as is and the same oracle
     built with FMA contraction (both correct) differ by up to 4e-11 (N=3) and
     2.4e-10 (N=4) per step and by 1.2e-8 after 40 steps on this trajectory.
-    So: every step's right-hand side to 1e-12 of the term scale; every step,
+    So: every step's right-hand side to 5e-14 of the term scale; every step,
     from the oracle's state, to 1e-9 relative; the whole run to 1e-6, with
     non-negative water height and conserved mass.
     """
@@ -224,11 +257,11 @@ def test_step_parity_thacker_ssp(N, rot):
     o, g = pair(p, **kw)
     W, _ = o.limit(p.W)
     W0 = W.copy()
-    worst_rhs, worst_step = 0.0, 0.0
+    worst_step = 0.0
     Wg_run = dev(W0)
     for _ in range(40):
         Ro = o.rhs(W)
-        worst_rhs = max(worst_rhs, rhs_err(g.rhs(dev(W)).cpu().numpy(), Ro, p, W))
+        check_rhs(g.rhs(dev(W)).cpu().numpy(), Ro, p, W, label=f"step {_}")
         Wo, rco, dto = o.step(W, 0.0, 1)
         Wg = dev(W)
         rcg, dtg = g.step(Wg, 0.0, 1)
@@ -237,7 +270,6 @@ def test_step_parity_thacker_ssp(N, rot):
         worst_step = max(worst_step, rel(Wg.cpu().numpy(), Wo))
         g.step(Wg_run, 0.0, 1)
         W = Wo
-    assert worst_rhs < RHS_TOL, worst_rhs
     assert worst_step < 1e-9, worst_step
     Wc = Wg_run.cpu().numpy()
     assert rel(Wc, W) < 1e-6
@@ -295,7 +327,7 @@ def test_rhs_full_size_dam_break_N7():
     o, g = pair(p, **kw)
     Ro = o.rhs(p.W)
     Rg = g.rhs(dev(p.W)).cpu().numpy()
-    assert rhs_err(Rg, Ro, p) < RHS_TOL
+    check_rhs(Rg, Ro, p)
     eo = o.epsilon()
     assert np.count_nonzero(eo) > 0
     assert np.abs(g.epsilon().cpu().numpy() - eo).max() < 1e-12
@@ -312,7 +344,7 @@ def test_rhs_full_size_degree_sweep(N):
         o, g = pair(p, **kw)
         Ro = o.rhs(p.W)
         Rg = g.rhs(dev(p.W)).cpu().numpy()
-        assert rhs_err(Rg, Ro, p) < RHS_TOL, kw
+        check_rhs(Rg, Ro, p, label=str(kw))
 
 
 def test_step_full_size_dam_break_N7():

@@ -48,3 +48,16 @@ def test_noalloc_rejects_too_many_elements():
     rc = lib.swe_integrals_noalloc(3, K, ptr, ptr, ptr, 9.81, ptr, ctypes.c_void_p(0))
     assert rc == swedg.ERR_ARG
     assert b"exceeds" in lib.swe_last_error()
+
+
+def test_noalloc_rejects_host_memory():
+    """A host pointer is refused before any launch (the kernels would read
+    it as a device address)."""
+    from paper_1804_02221_gb300 import swedg
+    lib = swedg.lib()
+    host = np.zeros(3 * 4 * 16)
+    dev = torch.zeros(3 * 4 * 16, dtype=torch.float64, device="cuda")
+    hp, dp = ctypes.c_void_p(host.ctypes.data), ctypes.c_void_p(dev.data_ptr())
+    rc = lib.swe_integrals_noalloc(3, 4, hp, dp, dp, 9.81, dp, ctypes.c_void_p(0))
+    assert rc == swedg.ERR_ARG
+    assert b"W" in lib.swe_last_error()
