@@ -47,6 +47,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-clocks", action="store_true")
     ap.add_argument("--no-autotune", action="store_true", help="keep the default launch shapes")
+    ap.add_argument("--no-developed", action="store_true",
+                    help="skip the leg timed from the developed state (200 steps after the dam release)")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the split-form vs standard-form comparison")
     ap.add_argument("--ensemble", type=int, default=0,
@@ -185,11 +187,11 @@ def combine_ranks(ms_step, e2e_ms, nodes, world_size, dist=None, device="cpu"):
 # Oracle timing (CPU baseline and reference arm)
 # ---------------------------------------------------------------------------
 
-def oracle_rate(N, K1, steps, warmup=0):
+def oracle_rate(N, K1, steps, warmup=0, variant=None, prob=None):
     from oracle import oracle as O
     from paper_1804_02221_gb300 import inputs as I
-    p = I.dam_break(N=N, K1=K1)
-    o = O.Oracle(p, flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    p = prob if prob is not None else I.dam_break(N=N, K1=K1)
+    o = O.Oracle(p, flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5, variant=variant)
     for _ in range(warmup):
         o.step(p.W, 0.0, 1)
         o.entropy(p.W)
@@ -199,7 +201,7 @@ def oracle_rate(N, K1, steps, warmup=0):
         o.entropy(W)
         o.mass(W)
     t = (time.perf_counter() - t0) / max(steps, 1)
-    return RK_STAGES * p.nodes / t, t, O.threads(), p.nodes
+    return RK_STAGES * p.nodes / t, t, O.threads(variant), p.nodes
 
 
 def cpu_model():
@@ -222,18 +224,23 @@ def cpu_model():
 
 
 def run_reference(args):
+    """The oracle on the host cores, on the GPU arm's own workload (the full
+    N=7 256x256 dam break unless --N/--K1 say otherwise): `steps` full
+    LSRK4(5) steps after `warmup` untimed ones, each step followed by the
+    mass and entropy of the new state."""
     ws, rank, _ = dist_env()
     if rank != 0:
         return
     N = args.N
-    K1 = 64  # bounded sample: same degree and recipe on 64x64 quads (262k nodes)
+    K1 = args.K1 or int(round(2048 / (N + 1)))
     rate, t, cores, nodes = oracle_rate(N, K1, args.steps, args.warmup)
-    sample = f"dam_break N={N} on {K1}x{K1} quads ({nodes} nodes), {args.steps} full LSRK4(5) steps"
+    sample = (f"dam_break N={N} on {K1}x{K1} quads ({nodes} nodes, the GPU arm's workload), "
+              f"{args.steps} full LSRK4(5) steps after {args.warmup} untimed, {t:.2f} s per step")
     line = {"impl": "reference", "metric": "RHS node-updates/s (FP64)", "value": rate,
             "unit": "node-updates/s", "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": workload_config(N, 2048 // (N + 1) if args.K1 is None else args.K1),
+            "config": workload_config(N, K1),
             "cpu_baseline": {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
                              "sample": sample, "cpu_model": cpu_model()},
             "e2e": {"value": rate, "unit": "node-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -555,6 +562,109 @@ def adjoint_bench(args):
     print(json.dumps(line), flush=True)
 
 
+def e2e_pipelined(ctx, Wh, W, steps, res, res_h, barrier):
+    """End to end through the C ABI from pinned host memory: each step's
+    state uploaded on a copy stream into the other of two device buffers
+    while the previous step computes (the upload into a buffer waits for the
+    step that last read it), the step's integrals, step size and status
+    copied back to pinned host memory. Returns ms per step (host clock)."""
+    import torch
+    stream = torch.cuda.current_stream()
+    Wb = [W, torch.empty_like(W)]
+    cs = torch.cuda.Stream()
+    arrived = [torch.cuda.Event(), torch.cuda.Event()]
+    freed = [torch.cuda.Event(), torch.cuda.Event()]
+    res_h.zero_()
+    torch.cuda.synchronize()
+    barrier()
+    t0 = time.perf_counter()
+    with torch.cuda.stream(cs):
+        Wb[0].copy_(Wh, non_blocking=True)
+        arrived[0].record(cs)
+    for i in range(steps):
+        cur = i % 2
+        stream.wait_event(arrived[cur])
+        if i + 1 < steps:
+            with torch.cuda.stream(cs):
+                if i >= 1:
+                    cs.wait_event(freed[1 - cur])
+                Wb[1 - cur].copy_(Wh, non_blocking=True)
+                arrived[1 - cur].record(cs)
+        ctx.step_async(Wb[cur], 0.0, 1, out=res[i])
+        res_h[i].copy_(res[i], non_blocking=True)
+        freed[cur].record(stream)
+    torch.cuda.synchronize()
+    return (time.perf_counter() - t0) * 1e3 / steps
+
+
+def viscous_fraction(ctx, W, R):
+    """Share of the elements with a nonzero viscosity in the right-hand side of W."""
+    ctx.rhs(W, R)
+    return float((ctx.epsilon() > 0).double().mean())
+
+
+def developed_leg(prob, W0, args, shapes, barrier, advance=200, cfl_visc=0.25, all_viscous=False):
+    """The same workload in a developed state: the dam break advanced
+    `advance` adaptive steps under the viscous time-step restriction
+    (cfl_visc; under the paper's rule alone this run's time step collapses),
+    then `steps` timed steps each restarting from that state, with the same
+    device-timed and end-to-end loops as the t = 0 line. all_viscous: the
+    indicator thresholds set so that every element carries eps0 (the upper
+    bound of the viscous work), timed from the start state (advance 0)."""
+    import torch
+
+    from paper_1804_02221_gb300 import swedg
+    stream = torch.cuda.current_stream()
+    kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5, cfl_visc=cfl_visc)
+    if all_viscous:
+        kw.update(sigma_min=-301.0, sigma_max=-300.0)
+    ctx = swedg.SweContext.from_problem(prob, **kw)
+    ctx.set_tuning(*shapes)
+    Wd = W0.clone()
+    adv = torch.zeros((max(advance, 1), 6), dtype=torch.float64, device="cuda")
+    for i in range(advance):
+        ctx.step_async(Wd, 0.0, 1, out=adv[i])
+    torch.cuda.synchronize()
+    a = adv[:advance].cpu()
+    if int((a[:, 5] != 0).sum()):
+        raise RuntimeError("the developed state's advance failed")
+    R = torch.empty_like(W0)
+    frac = viscous_fraction(ctx, Wd, R)
+    W = torch.empty_like(W0)
+    for _ in range(args.warmup):
+        W.copy_(Wd)
+        ctx.step_async(W, 0.0, 1)
+    res = torch.zeros((args.steps, 6), dtype=torch.float64, device="cuda")
+    res_h = torch.zeros((args.steps, 6), dtype=torch.float64).pin_memory()
+    ctx.timing(True, classes=("volume",))
+    torch.cuda.synchronize()
+    barrier()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for i in range(args.steps):
+        W.copy_(Wd)
+        ctx.step_async(W, 0.0, 1, out=res[i])
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    r = res.cpu()
+    if int((r[:, 5] != 0).sum()):
+        raise RuntimeError("a timed step from the developed state failed")
+    ms = e0.elapsed_time(e1) / args.steps
+    vol_ms, vol_n = ctx.timing_read("volume")
+    ctx.timing(False)
+    Wh = Wd.cpu().pin_memory()
+    e2e_ms = e2e_pipelined(ctx, Wh, W, args.steps, res, res_h, barrier)
+    if int((res_h[:, 5] != 0).sum()):
+        raise RuntimeError("an end-to-end step from the developed state failed")
+    out = {"ms_per_step": ms, "volume_ms_per_launch": vol_ms / max(vol_n, 1),
+           "viscous_element_fraction": frac, "advanced_steps": advance,
+           "t": float(a[:, 4].sum()), "dt": float(r[0, 4]), "cfl_visc": cfl_visc,
+           "e2e_ms_per_step": e2e_ms}
+    ctx.close()
+    return out
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -673,34 +783,8 @@ def main():
     e2e_serial_ms = (time.perf_counter() - t0) * 1e3 / args.steps
     check_steps(res_h)
 
-    # pipelined: the next step's input is uploaded on a copy stream into a
-    # second device buffer while the current step computes; the upload into
-    # a buffer waits for the step that last read it
-    Wb = [W, torch.empty_like(W0)]
-    cs = torch.cuda.Stream()
-    arrived = [torch.cuda.Event(), torch.cuda.Event()]
-    freed = [torch.cuda.Event(), torch.cuda.Event()]
-    res_h.zero_()
-    torch.cuda.synchronize()
-    barrier()
-    t0 = time.perf_counter()
-    with torch.cuda.stream(cs):
-        Wb[0].copy_(Wh, non_blocking=True)
-        arrived[0].record(cs)
-    for i in range(args.steps):
-        cur = i % 2
-        stream.wait_event(arrived[cur])
-        if i + 1 < args.steps:
-            with torch.cuda.stream(cs):
-                if i >= 1:
-                    cs.wait_event(freed[1 - cur])
-                Wb[1 - cur].copy_(Wh, non_blocking=True)
-                arrived[1 - cur].record(cs)
-        ctx.step_async(Wb[cur], 0.0, 1, out=res[i])
-        res_h[i].copy_(res[i], non_blocking=True)
-        freed[cur].record(stream)
-    torch.cuda.synchronize()
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / args.steps
+    # pipelined: the next step's input uploaded on a copy stream (e2e_pipelined)
+    e2e_ms = e2e_pipelined(ctx, Wh, W, args.steps, res, res_h, barrier)
     check_steps(res_h)
 
     # ---- RHS alone: entropy-conservative vs entropy-stable + AV ----
@@ -715,9 +799,19 @@ def main():
     # ---- the paper's comparison: split-form vs standard volume kernel ----
     cmp = None if args.no_compare else split_vs_standard(prob, W0, R)
 
+    # ---- the viscous share of the t = 0 state, and the developed state ----
+    visc0 = viscous_fraction(ctx, W0, R)
+    dev = None if args.no_developed else developed_leg(prob, W0, args, shapes, barrier)
+    allv = None if args.no_developed else developed_leg(prob, W0, args, shapes, barrier, advance=0,
+                                                         all_viscous=True)
+
     # ---- reduce over ranks ----
     t_step, e2e_ms, value, e2e_value = combine_ranks(ms, e2e_ms, nodes, ws, dist, "cuda")
     _, e2e_serial_ms, _, e2e_serial_value = combine_ranks(ms, e2e_serial_ms, nodes, ws, dist, "cuda")
+    for leg in (dev, allv):
+        if leg is not None:
+            leg["ms_per_step"], leg["e2e_ms_per_step"], leg["value"], leg["e2e_value"] = combine_ranks(
+                leg["ms_per_step"], leg["e2e_ms_per_step"], nodes, ws, dist, "cuda")
 
     if rank != 0:
         if dist is not None:
@@ -734,7 +828,7 @@ def main():
         "metric": "RHS node-updates/s (FP64)", "value": value, "unit": "node-updates/s",
         "n_gpus": ws, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_step,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-        "data": "synthetic", "config": workload_config(N, K1),
+        "data": "synthetic", "config": dict(workload_config(N, K1), viscous_element_fraction=visc0),
         "roofline": {"bound": "alu", "kernel": "volume", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
                      "ms_per_launch": vol_avg_ms, "flops_per_launch": flops,
@@ -760,20 +854,64 @@ def main():
         "split_vs_standard": cmp,
         "scalar_updates_per_s": 3 * value,
     }
+    if dev is not None:
+        # the same workload 200 steps after the dam release (viscous time-step
+        # restriction on, which keeps that run stable); the headline stays t = 0
+        dvol = dev["volume_ms_per_launch"]
+        line["developed"] = {
+            "value": dev["value"], "unit": "node-updates/s",
+            "ms_per_step": dev["ms_per_step"],
+            "e2e": {"value": dev["e2e_value"],
+                    "ms_per_step": dev["e2e_ms_per_step"], "h2d_bytes_per_step": int(W0.numel() * 8),
+                    "d2h_bytes_per_step": 6 * 8},
+            "viscous_element_fraction": dev["viscous_element_fraction"],
+            "roofline": {"bound": "alu", "kernel": "volume", "ms_per_launch": dvol,
+                         "achieved": flops / (dvol * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (dvol * 1e-3) / 1e12 / peak,
+                         "note": "algorithmic flops of the inviscid pair loop; the viscous divergence of "
+                                 "the viscous elements is extra work not counted"},
+            "state": {"advanced_steps": dev["advanced_steps"], "t": dev["t"], "dt": dev["dt"],
+                      "cfl_visc": dev["cfl_visc"]},
+            "config": {"workload": workload_config(N, K1)["workload"] + ", 200 steps after the dam release, "
+                                                                         "viscous time-step restriction cfl_visc=0.25"}}
+    if allv is not None:
+        avol = allv["volume_ms_per_launch"]
+        line["all_viscous"] = {
+            "value": allv["value"], "unit": "node-updates/s", "ms_per_step": allv["ms_per_step"],
+            "e2e": {"value": allv["e2e_value"], "ms_per_step": allv["e2e_ms_per_step"],
+                    "h2d_bytes_per_step": int(W0.numel() * 8), "d2h_bytes_per_step": 6 * 8},
+            "viscous_element_fraction": allv["viscous_element_fraction"],
+            "roofline": {"bound": "alu", "kernel": "volume", "ms_per_launch": avol,
+                         "achieved": flops / (avol * 1e-3) / 1e12, "peak": peak, "unit": "TFLOP/s",
+                         "frac": flops / (avol * 1e-3) / 1e12 / peak,
+                         "note": "inviscid algorithmic flops only (a lower bound of the work done)"},
+            "config": {"workload": workload_config(N, K1)["workload"] + ", every element at eps0 (upper bound "
+                                                                         "of the viscous work), cfl_visc=0.25"}}
     if not args.no_cpu_baseline and ws == 1:
         from oracle import oracle as O
-        rate, t, cores, n_s = oracle_rate(N, K1, 1)
+        rate, t, cores, n_s = oracle_rate(N, K1, 1, prob=prob)
         # the same oracle on one thread, on a bounded sample (64x64 quads)
         O.set_threads(1)
         rate1, t1, _, n_1 = oracle_rate(N, 64, 1)
         O.set_threads(cores)
+        # the same source built for speed only (timing; its results are not used)
+        tuned = None
+        try:
+            rate_t, t_t, cores_t, _ = oracle_rate(N, K1, 1, variant="tuned", prob=prob)
+            tuned = {"value": rate_t, "unit": "node-updates/s", "cores": cores_t,
+                     "flags": " ".join(O._flags("tuned")),
+                     "sample": f"one LSRK4(5) step of the same workload, {t_t:.2f} s"}
+        except Exception as exc:  # a host compiler without these flags: report why
+            tuned = {"unavailable": str(exc).splitlines()[0][:200]}
         line["cpu_baseline"] = {"value": rate, "unit": "node-updates/s", "cores": cores, "kind": "oracle",
                                 "sample": f"one LSRK4(5) step of the same workload ({n_s} nodes), "
                                           f"{t:.1f} s on {cores} OpenMP threads",
                                 "cpu_model": cpu_model(),
+                                "flags": " ".join(O._flags(None)),
                                 "single_thread": {"value": rate1, "unit": "node-updates/s",
                                                   "sample": f"one LSRK4(5) step, dam_break N={N} on 64x64 "
-                                                            f"quads ({n_1} nodes), {t1:.1f} s on 1 thread"}}
+                                                            f"quads ({n_1} nodes), {t1:.1f} s on 1 thread"},
+                                "tuned_build": tuned}
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

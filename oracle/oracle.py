@@ -21,19 +21,41 @@ LIB = os.path.join(HERE, "_build", "liborc.so")
 OK, ERR_ARG, ERR_GEOM, ERR_NEG_MEAN, ERR_NONFINITE = 0, -1, -2, -3, -4
 
 
-def build(force: bool = False) -> str:
+def _flags(variant):
+    """Compiler flags of a build variant. The default build is the checker:
+    no FMA contraction, so x86-64 and aarch64 give the same results. The
+    "tuned" build exists only to time the oracle as fast as the host compiler
+    makes it (FMA contraction, -O3, the host's own CPU target on aarch64); its
+    results are never compared with anything."""
+    if variant is None:
+        return ["-O2", "-ffp-contract=off"]
+    if variant == "tuned":
+        import platform
+        f = ["-O3", "-ffp-contract=fast"]
+        if platform.machine() == "aarch64":
+            f.append("-mcpu=native")
+        return f
+    raise ValueError(f"unknown oracle build variant {variant!r}")
+
+
+def lib_path(variant=None) -> str:
+    return LIB if variant is None else os.path.join(HERE, "_build", f"liborc_{variant}.so")
+
+
+def build(force: bool = False, variant=None) -> str:
     """Compile orc.c into _build/liborc.so (gcc, OpenMP, no FMA contraction so
-    that results agree between x86-64 and aarch64 hosts)."""
-    os.makedirs(os.path.dirname(LIB), exist_ok=True)
-    stale = (not os.path.exists(LIB) or
-             os.path.getmtime(LIB) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
+    that results agree between x86-64 and aarch64 hosts), or the timing-only
+    variant into _build/liborc_<variant>.so."""
+    path = lib_path(variant)
+    os.makedirs(os.path.dirname(path), exist_ok=True)
+    stale = (not os.path.exists(path) or
+             os.path.getmtime(path) < max(os.path.getmtime(SRC), os.path.getmtime(HDR)))
     if force or stale:
-        tmp = LIB + f".tmp{os.getpid()}"
-        cmd = ["gcc", "-std=c11", "-O2", "-fPIC", "-shared", "-fopenmp", "-ffp-contract=off",
-               "-o", tmp, SRC, "-lm"]
+        tmp = path + f".tmp{os.getpid()}"
+        cmd = ["gcc", "-std=c11"] + _flags(variant) + ["-fPIC", "-shared", "-fopenmp", "-o", tmp, SRC, "-lm"]
         subprocess.run(cmd, check=True)
-        os.replace(tmp, LIB)
-    return LIB
+        os.replace(tmp, path)
+    return path
 
 
 class Params(ctypes.Structure):
@@ -43,17 +65,15 @@ class Params(ctypes.Structure):
                 ("cfl", ctypes.c_double), ("volume", ctypes.c_int), ("cfl_visc", ctypes.c_double)]
 
 
-_lib = None
+_libs = {}
 
 
-def lib():
-    global _lib
-    if _lib is None:
-        _lib = ctypes.CDLL(build())
+def lib(variant=None):
+    if variant not in _libs:
+        L = ctypes.CDLL(build(variant=variant))
         dp = ctypes.POINTER(ctypes.c_double)
         ip = ctypes.POINTER(ctypes.c_int)
         vp = ctypes.c_void_p
-        L = _lib
         L.orc_basis.argtypes = [ctypes.c_int, dp, dp, dp, dp, dp]
         L.orc_create.argtypes = [ctypes.c_int, ctypes.c_int, dp, dp, ip, ip, ip, dp, ctypes.c_double,
                                  ctypes.POINTER(Params), ctypes.POINTER(vp)]
@@ -75,9 +95,12 @@ def lib():
                                        ctypes.c_double, ctypes.c_double, ctypes.c_double, dp]
         L.orc_surface_flux.restype = None
         L.orc_threads.argtypes = []
+        L.orc_set_threads.argtypes = [ctypes.c_int]
+        L.orc_set_threads.restype = None
         L.orc_lsrk_coefficients.argtypes = [dp, dp]
         L.orc_lsrk_coefficients.restype = None
-    return _lib
+        _libs[variant] = L
+    return _libs[variant]
 
 
 def _p(a: np.ndarray):
@@ -118,21 +141,22 @@ def lsrk_coefficients():
     return A, B
 
 
-def threads() -> int:
-    return lib().orc_threads()
+def threads(variant=None) -> int:
+    return lib(variant).orc_threads()
 
 
-def set_threads(t: int) -> None:
+def set_threads(t: int, variant=None) -> None:
     """OpenMP threads of later oracle calls (for timing the oracle)."""
-    lib().orc_set_threads(int(t))
+    lib(variant).orc_set_threads(int(t))
 
 
 class Oracle:
     """Oracle instance for one Problem (see paper_1804_02221_gb300.inputs)."""
 
     def __init__(self, prob, flux=1, av=False, eps0=0.0, sigma_min=math.nan, sigma_max=math.nan,
-                 limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0, cfl_visc=0.0):
+                 limiter=False, h_tol=math.nan, rk=0, cfl=0.5, volume=0, cfl_visc=0.0, variant=None):
         self.prob = prob
+        self._L = lib(variant)
         self.N, self.K, self.n = prob.N, prob.K, prob.N + 1
         self.params = Params(int(flux), int(av), float(eps0), float(sigma_min), float(sigma_max),
                              int(limiter), float(h_tol), int(rk), float(cfl), int(volume), float(cfl_visc))
@@ -143,7 +167,7 @@ class Oracle:
         self._F = np.ascontiguousarray(prob.EToF, dtype=np.int32)
         self._fl = np.ascontiguousarray(prob.flip, dtype=np.int32)
         h = ctypes.c_void_p()
-        rc = lib().orc_create(self.N, self.K, _p(self._x), _p(self._y), _p(self._E), _p(self._F),
+        rc = self._L.orc_create(self.N, self.K, _p(self._x), _p(self._y), _p(self._E), _p(self._F),
                               _p(self._fl), _p(self._b), float(prob.g), ctypes.byref(self.params),
                               ctypes.byref(h))
         if rc:
@@ -152,8 +176,8 @@ class Oracle:
 
     def __del__(self):
         h = getattr(self, "_h", None)
-        if h is not None and h.value and _lib is not None:
-            _lib.orc_destroy(h)
+        if h is not None and h.value and getattr(self, "_L", None) is not None:
+            self._L.orc_destroy(h)
             self._h = None
 
     def _W(self, W):
@@ -164,59 +188,59 @@ class Oracle:
     def geometry(self):
         shp = (self.K, self.n, self.n)
         out = [np.zeros(shp) for _ in range(5)]
-        lib().orc_geometry(self._h, *[_p(a) for a in out])
+        self._L.orc_geometry(self._h, *[_p(a) for a in out])
         return dict(zip(("x_xi", "x_eta", "y_xi", "y_eta", "J"), out))
 
     def rhs(self, W):
         W = self._W(W)
         R = np.zeros_like(W)
-        rc = lib().orc_rhs(self._h, _p(W), _p(R))
+        rc = self._L.orc_rhs(self._h, _p(W), _p(R))
         if rc:
             raise RuntimeError(f"orc_rhs rc={rc}")
         return R
 
     def epsilon(self):
         e = np.zeros(self.K)
-        lib().orc_get_epsilon(self._h, _p(e))
+        self._L.orc_get_epsilon(self._h, _p(e))
         return e
 
     def av_fields(self, W):
         W = self._W(W)
         eps = np.zeros(self.K)
         grads = np.zeros((4, self.K, self.n, self.n))
-        lib().orc_av_fields(self._h, _p(W), _p(eps), _p(grads))
+        self._L.orc_av_fields(self._h, _p(W), _p(eps), _p(grads))
         return eps, grads
 
     def limit(self, W):
         W = self._W(W).copy()
-        rc = lib().orc_limit(self._h, _p(W))
+        rc = self._L.orc_limit(self._h, _p(W))
         return W, rc
 
     def max_dt(self, W):
         W = self._W(W)
         dc, dp = ctypes.c_double(), ctypes.c_double()
-        lib().orc_max_dt(self._h, _p(W), ctypes.byref(dc), ctypes.byref(dp))
+        self._L.orc_max_dt(self._h, _p(W), ctypes.byref(dc), ctypes.byref(dp))
         return dc.value, dp.value
 
     def step(self, W, dt=0.0, nsteps=1):
         W = self._W(W).copy()
         dl = ctypes.c_double(0.0)
-        rc = lib().orc_step(self._h, _p(W), float(dt), int(nsteps), ctypes.byref(dl))
+        rc = self._L.orc_step(self._h, _p(W), float(dt), int(nsteps), ctypes.byref(dl))
         return W, rc, dl.value
 
     def mass(self, W):
         out = np.zeros(3)
-        lib().orc_mass(self._h, _p(self._W(W)), _p(out))
+        self._L.orc_mass(self._h, _p(self._W(W)), _p(out))
         return out
 
     def entropy_rate(self, W):
         """(rate, scale): sum J w w q(W).R(W) and sum J w w |q_c R_c|."""
         r, sc = ctypes.c_double(), ctypes.c_double()
-        rc = lib().orc_entropy_rate(self._h, _p(self._W(W)), ctypes.byref(r), ctypes.byref(sc))
+        rc = self._L.orc_entropy_rate(self._h, _p(self._W(W)), ctypes.byref(r), ctypes.byref(sc))
         assert rc == OK
         return r.value, sc.value
 
     def entropy(self, W):
         e = ctypes.c_double()
-        lib().orc_entropy(self._h, _p(self._W(W)), ctypes.byref(e))
+        self._L.orc_entropy(self._h, _p(self._W(W)), ctypes.byref(e))
         return e.value

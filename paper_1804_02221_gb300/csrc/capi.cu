@@ -383,7 +383,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     AL(W.uv, 2 * KN) AL(W.Fout, 3 * KS) AL(W.Ustar, 2 * KS) AL(W.eps, K) AL(W.Kreg, 3 * KN)
     AL(W.Wn, 3 * KN) AL(W.R, 3 * KN) AL(W.part, 4 * RED_BLOCKS + 8) AL(W.dt, 3 * (size_t)m.ninst + 1)
     if (p->av) {
-        AL(W.Fvt, 4 * KN) AL(W.Fvtr, 4 * KS) AL(W.Fvout, 2 * KS)
+        AL(W.Fvt, 4 * KN) AL(W.Fvtr, 4 * KS) AL(W.Fvout, 2 * KS) AL(W.Lv, 2 * KN)
     }
 #undef AL
     {

@@ -2,8 +2,13 @@
 // epsilon_k (App. A), then, only where epsilon_k > 0, the BR1 gradients of u
 // and v (Eq. BR1, strong form with the (U* - u) lift on the outward normal)
 // and the viscous fluxes F^v = h eps (U1, V1), G^v = h eps (U2, V2)
-// (Thm. 1), with their contravariant forms for the volume kernel and their
-// values at the element's side nodes for the interface average.
+// (Thm. 1), with their contravariant forms F~v, G~v, their values at the
+// element's side nodes for the interface average, and the volume part of the
+// viscous divergence of Eq. ViscTermsDisc, L^v = sum_q D_iq F~v_(q,j) +
+// D_jq G~v_(i,q), which the volume kernel adds (weighted by -w_i w_j) to the
+// viscous elements' nodes: computed here by the warp that owns the element,
+// so that the volume kernel's blocks stay balanced whether or not they hold
+// viscous elements.
 //
 // Indicator without the full modal transform. With Qhat = Vinv Q Vinv^T the
 // three energies of Eq. sigmadof are
@@ -39,6 +44,7 @@ struct AvArgs {
     const double* Ustar;
     double* Fvt;
     double* Fvtr;
+    double* Lv;
     double* eps;
     EpsParams ep;
     const int* stop;
@@ -101,6 +107,7 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
     __shared__ double sP[AV_WPB][AV_EPW][P4];
     __shared__ double sS[AV_WPB][AV_EPW][9];
     __shared__ double sUV[AV_WPB][2][nn];
+    __shared__ double sFv[AV_WPB][4][nn];
     __shared__ double sEps[AV_WPB][AV_EPW];
     if (stopped(a.stop)) return;
     const DeviceMesh& m = a.m;
@@ -246,10 +253,16 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
             const double G2 = he * fma(axy, ux, aey * ue);  // h eps U2
             const double F3 = he * fma(axx, vx, aex * ve);  // h eps V1
             const double G3 = he * fma(axy, vx, aey * ve);  // h eps V2
-            a.Fvt[gid] = fma(axx, F2, axy * G2);
-            a.Fvt[KN + gid] = fma(axx, F3, axy * G3);
-            a.Fvt[2 * KN + gid] = fma(aex, F2, aey * G2);
-            a.Fvt[3 * KN + gid] = fma(aex, F3, aey * G3);
+            const double ft2 = fma(axx, F2, axy * G2), ft3 = fma(axx, F3, axy * G3);
+            const double gt2 = fma(aex, F2, aey * G2), gt3 = fma(aex, F3, aey * G3);
+            a.Fvt[gid] = ft2;
+            a.Fvt[KN + gid] = ft3;
+            a.Fvt[2 * KN + gid] = gt2;
+            a.Fvt[3 * KN + gid] = gt3;
+            sFv[w][0][node] = ft2;
+            sFv[w][1][node] = ft3;
+            sFv[w][2][node] = gt2;
+            sFv[w][3][node] = gt3;
             auto put = [&](int f, int p) {
                 const long long sl = side + f * n + p;
                 a.Fvtr[sl] = F2;
@@ -261,6 +274,26 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
             if (i == N) put(1, j);
             if (j == N) put(2, i);
             if (i == 0) put(3, j);
+        }
+        __syncwarp();
+        // volume part of the viscous divergence (the contravariant fluxes of
+        // all the element's nodes are in shared memory now)
+#pragma unroll 1
+        for (int r = 0; r < PER; ++r) {
+            const int node = lane + 32 * r;
+            if (node >= nn) continue;
+            const int i = node % n, j = node / n;
+            double L2 = 0.0, L3 = 0.0;
+#pragma unroll
+            for (int q = 0; q < n; ++q) {
+                const double di = sD[i * n + q], dj = sD[j * n + q];
+                L2 = fma(di, sFv[w][0][j * n + q], L2);
+                L3 = fma(di, sFv[w][1][j * n + q], L3);
+                L2 = fma(dj, sFv[w][2][q * n + i], L2);
+                L3 = fma(dj, sFv[w][3][q * n + i], L3);
+            }
+            a.Lv[base + node] = L2;
+            a.Lv[KN + base + node] = L3;
         }
         __syncwarp();
     }
@@ -290,7 +323,7 @@ EpsParams eps_params(const swe_ctx* c) {
 }
 
 void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given) {
-    AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.eps, eps_params(c), stop};
+    AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.Lv, c->w.eps, eps_params(c), stop};
     switch (c->m.N) {
         case 1: av_n<1>(c, a, s, eps_given); break;
         case 2: av_n<2>(c, a, s, eps_given); break;

@@ -31,6 +31,11 @@
 //    through shared memory, then runs the eta-line with the same index
 //    starting from them, and finishes the nodes of that column (interface
 //    lifts, viscous terms, source, scaling by -1/(w_i w_j J)) in registers.
+//  * The volume part of the viscous divergence (sum_q D_iq F~v + D_jq G~v)
+//    of the few viscous elements comes from the AV kernel (Lv); here it is
+//    weighted by -w_i w_j and added, with the viscous interface lifts. A
+//    block holding a viscous element then costs what the others cost, and
+//    the AV variant stages nothing more than the inviscid one.
 //    The loops are fully unrolled: all pair indices are compile-time.
 //  * Launch shapes: blocks of TPB/(N+1) elements (TPB = 64, 128, 256), one
 //    translation unit per shape; every shape computes every element with the
@@ -42,11 +47,8 @@
 namespace swe {
 namespace {
 
-// Shared-memory planes of the staged elements. After the eta pass, blocks
-// with viscous elements reuse the planes of hu, hv, u, v for the
-// contravariant viscous fluxes.
+// Shared-memory planes of the staged elements.
 enum { F_H, F_HU, F_HV, F_U, F_V, F_P, F_A1, F_A2, F_A3, F_COUNT };
-enum { F_FT2 = F_HU, F_FT3 = F_HV, F_GT2 = F_U, F_GT3 = F_V };
 
 struct VolArgs {
     DeviceMesh m;
@@ -55,6 +57,7 @@ struct VolArgs {
     const double* Fout;
     const double* Fvt;
     const double* Fvout;
+    const double* Lv;
     const double* eps;
     double* R;
     const int* stop;
@@ -68,8 +71,7 @@ constexpr int vol_ne() {
 
 template <int N, bool AV, int TPB>
 constexpr size_t vol_smem() {
-    return sizeof(double) *
-           ((size_t)F_COUNT * vol_ne<N, TPB>() * (N + 1) * (N + 1) + (AV ? (N + 1) * (N + 1) : 0));
+    return sizeof(double) * ((size_t)F_COUNT * vol_ne<N, TPB>() * (N + 1) * (N + 1));
 }
 
 // Shapes whose staging exceeds the 227 KB of shared memory a block may use
@@ -167,7 +169,6 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     const int t = threadIdx.x;
     const long long k0 = (long long)blockIdx.x * NE;
     auto S = [&](int f) { return sm + f * BLK; };
-    double* sD = sm + F_COUNT * BLK;
 
     // ---- stage the block's elements ---------------------------------------
     const double g2 = 2.0 * m.g;
@@ -276,7 +277,6 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         }
     }
     // own-velocity parts of the momentum fluxes, then the mass flux 2 sum Q
-    // (before the viscous staging reuses the velocity planes)
 #pragma unroll
     for (int p = 0; p < n; ++p) {
         const int nd = e * nn + p * n + l;
@@ -285,25 +285,6 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         A1[p] += A1[p];
     }
 
-    // ---- viscous fluxes of the block's viscous elements --------------------
-    if (AV) {
-        const int any = __syncthreads_or(visc);
-        if (any) {
-            for (int idx = t; idx < BLK; idx += NT) {
-                const int ee = idx / nn;
-                const long long kk = k0 + ee;
-                if (kk < m.K && a.eps[kk] > 0.0) {
-                    const long long gid = kk * nn + (idx - ee * nn);
-                    S(F_FT2)[idx] = a.Fvt[gid];
-                    S(F_FT3)[idx] = a.Fvt[m.KN + gid];
-                    S(F_GT2)[idx] = a.Fvt[2 * m.KN + gid];
-                    S(F_GT3)[idx] = a.Fvt[3 * m.KN + gid];
-                }
-            }
-            for (int idx = t; idx < nn; idx += NT) sD[idx] = Dm<N>(idx / n, idx % n);
-        }
-        __syncthreads();
-    }
     if (!valid) return;
 
     // ---- nodes (i = l, j = p): lifts, viscous terms, source, scaling --------
@@ -325,20 +306,11 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         if (j == 0) lift(0, i, wi);
         if (j == N) lift(2, i, wi);
         if (AV) {
-            const int nd = eb + j * n + i;
             if (visc) {
-                double L2 = 0.0, L3 = 0.0;
-#pragma unroll
-                for (int q = 0; q < n; ++q) {
-                    const double di = sD[i * n + q], dj = Dm<N>(j, q);
-                    L2 = fma(di, S(F_FT2)[eb + j * n + q], L2);
-                    L3 = fma(di, S(F_FT3)[eb + j * n + q], L3);
-                    L2 = fma(dj, S(F_GT2)[eb + q * n + i], L2);
-                    L3 = fma(dj, S(F_GT3)[eb + q * n + i], L3);
-                }
+                // the volume part of the viscous divergence (AV kernel)
                 const double wij = wi * wq<N>(j);
-                a2 = fma(-wij, L2, a2);
-                a3 = fma(-wij, L3, a3);
+                a2 = fma(-wij, a.Lv[gid], a2);
+                a3 = fma(-wij, a.Lv[m.KN + gid], a3);
             }
             // viscous lift at sides 0 and 2: -(tangential weight) (F^v*_out -
             // own outward flux), skipped where no viscous flux reaches the face
@@ -346,7 +318,8 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
                 const long long sl = side + f * n + i;
                 const double fv2 = a.Fvout[sl], fv3 = a.Fvout[KS + sl];
                 if (visc || nonzero(fv2) || nonzero(fv3)) {
-                    const double own2 = visc ? sg * S(F_GT2)[nd] : 0.0, own3 = visc ? sg * S(F_GT3)[nd] : 0.0;
+                    const double own2 = visc ? sg * a.Fvt[2 * m.KN + gid] : 0.0;
+                    const double own3 = visc ? sg * a.Fvt[3 * m.KN + gid] : 0.0;
                     a2 = fma(-wi, fv2 - own2, a2);
                     a3 = fma(-wi, fv3 - own3, a3);
                 }
@@ -359,6 +332,139 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         a.R[gid] = f * a1;
         a.R[m.KN + gid] = fma(h, m.srcx[gid], f * a2);
         a.R[2 * m.KN + gid] = fma(h, m.srcy[gid], f * a3);
+    }
+}
+
+// Small degrees (N <= 2): one thread per element. With 4 or 9 nodes an
+// element's line holds one or three pairs, too little work between the line
+// kernel's staging and hand-over barriers to keep the FP64 pipe busy. Here a
+// thread holds its whole element in registers (state, velocities, the three
+// accumulators), runs the pairs of all its xi- and eta-lines back to back,
+// then adds the own-velocity parts, the interface lifts (tangential weight
+// times F_out, every side), the viscous terms and the source, and scales by
+// -1/(w_i w_j J): no shared memory and no barriers. The arithmetic of a pair
+// is the line kernel's (15 FP64 instructions); the block size (TPB elements)
+// is the launch shape, with the same instructions for every shape.
+template <int N>
+constexpr bool vol_ept() {
+    return N <= 2;
+}
+
+template <int N>
+__device__ __forceinline__ int side_node(int f, int p) {
+    return f == 0 ? p : (f == 1 ? p * (N + 1) + N : (f == 2 ? N * (N + 1) + p : p * (N + 1)));
+}
+
+template <int N, bool AV, int TPB>
+__global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
+    constexpr int n = N + 1, nn = n * n, NP = N * (N + 1) / 2;
+    if (stopped(a.stop)) return;
+    const DeviceMesh& m = a.m;
+    const long long k = (long long)blockIdx.x * TPB + threadIdx.x;
+    if (k >= m.K) return;
+    const long long g0 = k * nn;
+    const double g2 = 2.0 * m.g;
+    double h[nn], hu[nn], hv[nn], u[nn], v[nn], pp[nn], A1[nn], A2[nn], A3[nn];
+#pragma unroll
+    for (int d = 0; d < nn; ++d) {
+        h[d] = a.W[g0 + d];
+        hu[d] = a.W[m.KN + g0 + d];
+        hv[d] = a.W[2 * m.KN + g0 + d];
+        u[d] = a.uv[g0 + d];
+        v[d] = a.uv[m.KN + g0 + d];
+        pp[d] = g2 * h[d];
+        A1[d] = A2[d] = A3[d] = 0.0;
+    }
+    // pair constants of the element: [direction][pair][line][2]
+    const double* pm = m.pm + (size_t)k * 4 * NP * n;
+#pragma unroll
+    for (int dir = 0; dir < 2; ++dir) {
+#pragma unroll
+        for (int l = 0; l < n; ++l) {
+#pragma unroll
+            for (int i = 0; i < n; ++i) {
+#pragma unroll
+                for (int q = i + 1; q < n; ++q) {
+                    const int ni = dir == 0 ? l * n + i : i * n + l;
+                    const int nq = dir == 0 ? l * n + q : q * n + l;
+                    const int pr = pair_index<N>(i, q);
+                    const double2 c =
+                        __ldg(reinterpret_cast<const double2*>(pm + 2 * ((dir * NP + pr) * n + l)));
+                    const double Q = fma(hu[ni] + hu[nq], c.x, (hv[ni] + hv[nq]) * c.y);
+                    const double P = pp[ni] * h[nq];
+                    A1[ni] += Q;
+                    A1[nq] -= Q;
+                    A2[ni] = fma(P, c.x, fma(u[nq], Q, A2[ni]));
+                    A2[nq] = fma(-P, c.x, fma(-u[ni], Q, A2[nq]));
+                    A3[ni] = fma(P, c.y, fma(v[nq], Q, A3[ni]));
+                    A3[nq] = fma(-P, c.y, fma(-v[ni], Q, A3[nq]));
+                }
+            }
+        }
+    }
+    // own-velocity parts of the momentum fluxes, then the mass flux 2 sum Q
+#pragma unroll
+    for (int d = 0; d < nn; ++d) {
+        A2[d] = fma(u[d], A1[d], A2[d]);
+        A3[d] = fma(v[d], A1[d], A3[d]);
+        A1[d] += A1[d];
+    }
+    // interface flux: w_i w_j (1/w_0) F_out = (tangential weight) F_out
+    const long long side = k * 4 * n;
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+            const int d = side_node<N>(f, p);
+            const long long sl = side + f * n + p;
+            const double wt = wq<N>(p);
+            A1[d] = fma(wt, a.Fout[sl], A1[d]);
+            A2[d] = fma(wt, a.Fout[m.KS + sl], A2[d]);
+            A3[d] = fma(wt, a.Fout[2 * m.KS + sl], A3[d]);
+        }
+    }
+    if (AV) {
+        const bool visc = a.eps[k] > 0.0;
+        if (visc) {
+            // the volume part of the viscous divergence (AV kernel)
+#pragma unroll
+            for (int j = 0; j < n; ++j) {
+#pragma unroll
+                for (int i = 0; i < n; ++i) {
+                    const double wij = wq<N>(i) * wq<N>(j);
+                    A2[j * n + i] = fma(-wij, a.Lv[g0 + j * n + i], A2[j * n + i]);
+                    A3[j * n + i] = fma(-wij, a.Lv[m.KN + g0 + j * n + i], A3[j * n + i]);
+                }
+            }
+        }
+        // viscous lifts -(tangential weight) (F^v*_out - own outward flux),
+        // skipped where no viscous flux reaches the face (both sides inviscid)
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                const int d = side_node<N>(f, p);
+                const long long sl = side + f * n + p;
+                const double fv2 = a.Fvout[sl], fv3 = a.Fvout[m.KS + sl];
+                if (visc || nonzero(fv2) || nonzero(fv3)) {
+                    const double sg = (f == 1 || f == 2) ? 1.0 : -1.0;
+                    const long long pl = (f == 1 || f == 3) ? 0 : 2 * m.KN;  // F~v on xi sides, G~v on eta sides
+                    const double own2 = visc ? sg * a.Fvt[pl + g0 + d] : 0.0;
+                    const double own3 = visc ? sg * a.Fvt[pl + m.KN + g0 + d] : 0.0;
+                    const double wt = wq<N>(p);
+                    A2[d] = fma(-wt, fv2 - own2, A2[d]);
+                    A3[d] = fma(-wt, fv3 - own3, A3[d]);
+                }
+            }
+        }
+    }
+#pragma unroll
+    for (int d = 0; d < nn; ++d) {
+        const long long gid = g0 + d;
+        const double f = m.fwJ[gid];
+        a.R[gid] = f * A1[d];
+        a.R[m.KN + gid] = fma(h[d], m.srcx[gid], f * A2[d]);
+        a.R[2 * m.KN + gid] = fma(h[d], m.srcy[gid], f * A3[d]);
     }
 }
 
@@ -376,7 +482,11 @@ void set_attr() {
 
 template <int N, bool AV, int TPB>
 bool launch_n(swe_ctx* c, const VolArgs& a, cudaStream_t s) {
-    if constexpr (!vol_fits<N, AV, TPB>()) {
+    if constexpr (vol_ept<N>()) {
+        Timed tm(c, KC_VOLUME, s);
+        k_volume_ept<N, AV, TPB><<<grid_for(c->m.K, TPB), TPB, 0, s>>>(a);
+        return true;
+    } else if constexpr (!vol_fits<N, AV, TPB>()) {
         return false;
     } else {
         constexpr int NE = vol_ne<N, TPB>();
@@ -390,6 +500,7 @@ bool launch_n(swe_ctx* c, const VolArgs& a, cudaStream_t s) {
 
 template <int N, int TPB>
 bool prepare_n() {
+    if constexpr (vol_ept<N>()) return true;
     if constexpr (vol_fits<N, true, TPB>()) set_attr<N, true, TPB>();
     if constexpr (vol_fits<N, false, TPB>()) set_attr<N, false, TPB>();
     return vol_fits<N, true, TPB>() && vol_fits<N, false, TPB>();
@@ -410,7 +521,7 @@ bool prepare_shape(int N) {
 
 template <int TPB>
 bool launch_shape(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop) {
-    VolArgs a{c->m, W, c->w.uv, c->w.Fout, c->w.Fvt, c->w.Fvout, c->w.eps, R, stop};
+    VolArgs a{c->m, W, c->w.uv, c->w.Fout, c->w.Fvt, c->w.Fvout, c->w.Lv, c->w.eps, R, stop};
     const bool av = c->p.av != 0;
 #define SWE_VOL_CASE(NN) \
     case NN: return av ? launch_n<NN, true, TPB>(c, a, s) : launch_n<NN, false, TPB>(c, a, s);

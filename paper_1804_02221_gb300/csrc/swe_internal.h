@@ -132,6 +132,8 @@ struct Work {
     double* Fvtr;   // [4][KS] physical viscous fluxes at side nodes F2, F3, G2, G3
                     // (written for viscous elements only; read only for them)
     double* Fvout;  // [2][KS] outward viscous interface flux
+    double* Lv;     // [2][KN] volume part of the viscous divergence, sum_q D_iq F~v + D_jq G~v
+                    // (components 2, 3; written and read for viscous elements only)
     double* eps;    // [K]
     double* Kreg;   // [3][KN] 2N-storage register
     double* Wn;     // [3][KN] state at the start of a step
