@@ -163,6 +163,19 @@ def volume_traffic(N, nodes):
     return float(vals["traffic.dram_bytes_per_node"]) * nodes
 
 
+def volume_adjoint_flops_per_node(N):
+    """Algorithmic flops of the adjoint of the volume kernel (inviscid part):
+    per symmetric pair 38 (the three cotangent differences 3, the pair's
+    flux Q 5, its cotangent Q^ = 2 d1 + (u_i+u_q) d2 + (v_i+v_q) d3 7, the
+    pressure cotangent P^ = Sx d2 + Sy d3 3, ten cotangent accumulations
+    20), N pairs per node; per node 10 (the cotangents of R scaled by
+    -1/(w w J) 3, the h cotangent with the source terms 5, the source
+    coefficients' cotangents 2) and the interface-flux cotangents, 3
+    products on each of the 4(N+1) side nodes of an element."""
+    n = N + 1
+    return 38 * N + 10 + 3 * 4 * n / (n * n)
+
+
 def fp64_peak_gflops(sm_mhz):
     """152 SMs x 2 FP64 fused multiply-adds per clock (measured: 1.9 DFMA/clk/SM
     with independent chains at 2070 MHz nominal) x 2 flops."""
@@ -533,6 +546,24 @@ def adjoint_bench(args):
     cb.rhs_adjoint(Wd, Rbd, Wbd, bbd)
     ms_big, _ = timed(lambda: [cb.rhs(Wd, Rd) for _ in range(5)])
     ms_big_adj, _ = timed(lambda: [cb.rhs_adjoint(Wd, Rbd, Wbd, bbd) for _ in range(5)])
+    # the launch time of every kernel class within one right-hand-side adjoint
+    # (events around every launch: a pass of its own), and the reverse volume
+    # kernel against its algorithmic flops
+    cb.timing(True)
+    for _ in range(5):
+        cb.rhs_adjoint(Wd, Rbd, Wbd, bbd)
+    torch.cuda.synchronize()
+    adj_classes = {}
+    for name in swedg.KERNEL_CLASSES:
+        t, n_l = cb.timing_read(name)
+        if n_l:
+            adj_classes[name] = {"ms_per_rhs_adjoint": t / 5, "launches_per_rhs_adjoint": n_l / 5}
+    cb.timing(False)
+    vol_adj_ms = adj_classes["adjoint_volume"]["ms_per_rhs_adjoint"] / adj_classes["adjoint_volume"][
+        "launches_per_rhs_adjoint"]
+    vol_fwd_ms = kernel_ms(cb, Wd, Rd, "volume", reps=5)
+    fl_adj = volume_adjoint_flops_per_node(7) * big.nodes / (vol_adj_ms * 1e-3) / 1e12
+    peak = fp64_peak_gflops(2070.0) / 1e3
     cb.close()
     line = {
         "adjoint": True, "metric": "RHS node-updates/s (FP64)", "unit": "node-updates/s",
@@ -557,7 +588,14 @@ def adjoint_bench(args):
                   "rhs_ms": ms_big / 5, "rhs_adjoint_ms": ms_big_adj / 5,
                   "rhs_value": big.nodes / (ms_big / 5 * 1e-3),
                   "rhs_adjoint_value": big.nodes / (ms_big_adj / 5 * 1e-3),
-                  "ratio": ms_big_adj / ms_big},
+                  "ratio": ms_big_adj / ms_big,
+                  "rhs_adjoint_kernels": adj_classes,
+                  "volume_adjoint": {"ms_per_launch": vol_adj_ms, "forward_volume_ms_per_launch": vol_fwd_ms,
+                                     "ratio_to_forward": vol_adj_ms / vol_fwd_ms,
+                                     "flops_per_node": volume_adjoint_flops_per_node(7),
+                                     "roofline": {"bound": "alu", "achieved": fl_adj, "peak": peak,
+                                                  "unit": "TFLOP/s", "frac": fl_adj / peak,
+                                                  "peak_note": "152 SMs x 2 DFMA/clk x 2 flops at 2070 MHz"}}},
     }
     print(json.dumps(line), flush=True)
 

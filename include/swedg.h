@@ -200,7 +200,8 @@ int swe_status(swe_ctx* ctx, int* bits, void* stream);
  * every kernel launch is bracketed by CUDA events on its stream;
  * swe_timing_read returns, for kernel class `which` (0 volume, 1 interface
  * flux, 2 primitives, 3 AV indicator/gradient, 4 viscous interface, 5 stage
- * update/limiter, 6 time step, 7 reductions, 8 adjoint), the summed event time in
+ * update/limiter, 6 time step, 7 reductions, 8 adjoint kernels other than 9,
+ * 9 adjoint of the volume kernel), the summed event time in
  * milliseconds and the launch count since swe_timing(ctx, 1) (synchronises).
  * swe_launches returns the number of kernels the context launched so far. */
 int swe_timing(swe_ctx* ctx, int on);

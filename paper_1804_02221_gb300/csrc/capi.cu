@@ -395,6 +395,21 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         W.status = reinterpret_cast<int*>(static_cast<char*>(q) + 2 * sizeof(unsigned long long) * m.ninst);
         if (shared_status) W.status = shared_status;
     }
+    if (p->av) {
+        void* q = nullptr;
+        e2 = cudaMalloc(&q, (size_t)K + 16);
+        if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
+        c->allocations.push_back(q);
+        W.touch = static_cast<uint8_t*>(q);
+        cudaMemset(W.touch, 0, (size_t)K);
+        q = nullptr;
+        e2 = cudaMalloc(&q, sizeof(int) * ((size_t)K + 4));
+        if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
+        c->allocations.push_back(q);
+        W.vcount = static_cast<int*>(q);
+        W.vlist = W.vcount + 4;
+        cudaMemset(W.vcount, 0, sizeof(int) * ((size_t)K + 4));
+    }
     if (!shared_status) cudaMemset(W.status, 0, sizeof(int));
     swe::prepare_volume(c);
     cudaMemset(W.eps, 0, sizeof(double) * K);
@@ -778,13 +793,15 @@ int adjoint_args(swe_ctx* c, const void* W, const void* cot, const void* Wbar, c
 
 }  // namespace
 
-// The forward quantities the reverse sweep reads at W: velocities, BR1
-// interface values and, unless given, the element viscosities. The volume
-// term and the viscous fluxes themselves are not needed.
+// The forward quantities the reverse sweep reads at W: velocities and, with
+// the viscosity on, the BR1 interface values and (unless given) the element
+// viscosities with the BR1 gradients. The interface flux, the volume term
+// and the viscous interface average themselves are not needed.
 static void adjoint_prerequisites(swe_ctx* c, const double* W, cudaStream_t s, bool eps_given) {
     swe::launch_prim(c, W, s, nullptr);
-    swe::launch_surface(c, W, s, nullptr);
-    if (c->p.av && !eps_given) swe::launch_av(c, W, s, nullptr, false);
+    if (!c->p.av) return;
+    swe::launch_ustar(c, s);
+    if (!eps_given) swe::launch_av(c, W, s, nullptr, false);
 }
 
 extern "C" int swe_rhs_adjoint(swe_ctx* c, const double* W, const double* Rbar, double* Wbar, double* bbar,

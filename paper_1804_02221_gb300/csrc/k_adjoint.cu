@@ -1051,7 +1051,7 @@ void vol_adj_n(swe_ctx* c, const VolAdjArgs& a, cudaStream_t s) {
         cudaFuncSetAttribute(k_volume_adj<N, AV>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         attr = true;
     }
-    Timed tm(c, KC_ADJ, s);
+    Timed tm(c, KC_ADJ_VOL, s);
     k_volume_adj<N, AV><<<grid_for(c->m.K, adj_ne<N>()), adj_ne<N>() * (N + 1), smem, s>>>(a);
 }
 

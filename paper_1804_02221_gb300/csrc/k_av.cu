@@ -46,6 +46,8 @@ struct AvArgs {
     double* Fvtr;
     double* Lv;
     double* eps;
+    int* vlist;   // [K] the viscous elements of the state (indicator kernel), in no fixed order
+    int* vcount;  // their number
     EpsParams ep;
     const int* stop;
 };
@@ -93,30 +95,25 @@ __device__ __forceinline__ double epsilon_from_sums(const double* S, const EpsPa
            (1.0 + sin(3.14159265358979323846 * (sig - 0.5 * (ep.smax + ep.smin)) / (ep.smax - ep.smin)));
 }
 
-// EPS_GIVEN: epsilon of this state is already in the work buffer; only the
-// viscous fluxes remain.
-template <int N, bool EPS_GIVEN, bool WIDE>
+// The smoothness indicator and epsilon of every element; the viscous
+// elements are appended to a list (in no fixed order: every element's fluxes
+// are computed independently, so the results do not depend on it) for the
+// viscous-flux kernel.
+template <int N, bool WIDE>
 __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
     constexpr int AV_EPW = av_epw<N, WIDE>();
     constexpr int LPE = 32 / AV_EPW;  // lanes per element for the sums (4, 2 or 1)
     constexpr int SPL = 8 / LPE;      // projection sums per lane (2, 4 or 8)
-    constexpr int n = N + 1, nn = n * n, P4 = 4 * n, PER = (nn + 31) / 32;
-    constexpr double iw0 = N * (N + 1) / 2.0;
-    __shared__ double sD[nn], sVi[nn], sWW[nn];
+    constexpr int n = N + 1, nn = n * n, P4 = 4 * n;
+    __shared__ double sVi[nn], sWW[nn];
     __shared__ double sQ[AV_WPB][AV_EPW][nn];
     __shared__ double sP[AV_WPB][AV_EPW][P4];
     __shared__ double sS[AV_WPB][AV_EPW][9];
-    __shared__ double sUV[AV_WPB][2][nn];
-    __shared__ double sFv[AV_WPB][4][nn];
-    __shared__ double sEps[AV_WPB][AV_EPW];
     if (stopped(a.stop)) return;
     const DeviceMesh& m = a.m;
     for (int t = threadIdx.x; t < nn; t += blockDim.x) {
-        sD[t] = Dm<N>(t / n, t % n);
-        if (!EPS_GIVEN) {
-            sVi[t] = c_Vinv[mat_offset(N) + t];
-            sWW[t] = c_w[vec_offset(N) + t % n] * c_w[vec_offset(N) + t / n];
-        }
+        sVi[t] = c_Vinv[mat_offset(N) + t];
+        sWW[t] = c_w[vec_offset(N) + t % n] * c_w[vec_offset(N) + t / n];
     }
     __syncthreads();
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -124,113 +121,138 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
     if (k0 >= m.K) return;  // whole warps leave together; no block barrier follows
     const int ne = (int)((m.K - k0) < AV_EPW ? (m.K - k0) : AV_EPW);
     double(*Q)[nn] = sQ[w];
-
-    if (!EPS_GIVEN) {
-        // ---- water heights of the warp's elements (contiguous in memory) --
-        // a compile-time trip count, unrolled: the loads of all iterations
-        // are in flight together
-        constexpr int LQ = (AV_EPW * nn + 31) / 32;
+    // ---- water heights of the warp's elements (contiguous in memory) --
+    // a compile-time trip count, unrolled: the loads of all iterations
+    // are in flight together
+    constexpr int LQ = (AV_EPW * nn + 31) / 32;
 #pragma unroll
-        for (int r = 0; r < LQ; ++r) {
-            const int idx = lane + 32 * r;
-            if (idx < AV_EPW * nn) {
-                const int e = idx / nn;
-                Q[e][idx - e * nn] = e < ne ? a.W[k0 * nn + idx] : 0.0;
-            }
+    for (int r = 0; r < LQ; ++r) {
+        const int idx = lane + 32 * r;
+        if (idx < AV_EPW * nn) {
+            const int e = idx / nn;
+            Q[e][idx - e * nn] = e < ne ? a.W[k0 * nn + idx] : 0.0;
         }
-        __syncwarp();
-        // ---- the four projections of every element ------------------------
-        // AV_EPW n / 8 tasks per lane, unrolled: the lane's
-        // independent dot products interleave, instead of one dependent chain
-        // of fused multiply-adds at a time
-        static_assert((AV_EPW * P4) % 32 == 0, "projection tasks fill whole warps");
-#pragma unroll
-        for (int r = 0; r < AV_EPW * P4 / 32; ++r) {
-            const int s = lane + 32 * r;
-            const int e = s / P4, L = s - e * P4, t = L / n, p = L - t * n;
-            const double* vr = sVi + (t < 2 ? N : N - 1) * n;
-            // t even: sum over i at j = p; t odd: sum over j at i = p. One
-            // code path with an index stride, so that the lanes of a warp do
-            // not split into two half-empty FP64 instruction streams.
-            const int b0 = (t & 1) ? p : p * n, st = (t & 1) ? n : 1;
-            double v = 0.0;
-#pragma unroll
-            for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][b0 + q * st], v);
-            sP[w][e][L] = v;
-        }
-        // ---- sum w w Q^2: LPE lanes per element ----------------------------
-        const int e4 = lane / LPE, sub = lane % LPE;
-        double swq = 0.0;
-#pragma unroll
-        for (int r = 0; r < (nn + LPE - 1) / LPE; ++r) {
-            const int node = sub + LPE * r;
-            const double q = node < nn ? Q[e4][node] : 0.0;
-            swq = fma(sWW[node < nn ? node : 0] * q, q, swq);
-        }
-#pragma unroll
-        for (int o = 1; o < LPE; o <<= 1) swq += __shfl_xor_sync(0xffffffffu, swq, o);
-        __syncwarp();
-        // ---- the eight projection sums: SPL per lane -----------------------
-        // sum index m: 0..3 weighted squares of y_xi, y_eta, z_xi, z_eta;
-        // 4: B0 = Vinv[N].y_xi, 5: C0 = Vinv[N-1].y_xi, 6: B2 = Vinv[N].z_xi,
-        // 7: C2 = Vinv[N-1].z_xi; each written as sum_p (c_p x_p) y_p
-#pragma unroll
-        for (int h2 = 0; h2 < SPL; ++h2) {
-            const int mi = SPL * sub + h2;
-            const bool sq = mi < 4;
-            const double* x = sP[w][e4] + (sq ? mi : (mi < 6 ? 0 : 2)) * n;
-            const double* c = sVi + ((mi & 1) == 0 ? N : N - 1) * n;
-            double s = 0.0;
-#pragma unroll
-            for (int p = 0; p < n; ++p) {
-                const double cp = sq ? c_w[vec_offset(N) + p] : c[p];
-                const double yp = sq ? x[p] : 1.0;
-                s = fma(cp * x[p], yp, s);
-            }
-            sS[w][e4][mi] = s;
-        }
-        if (sub == 0) sS[w][e4][8] = swq;
-        __syncwarp();
-        // ---- epsilon, one lane per element --------------------------------
-        if (lane < AV_EPW) {
-            const double ep = epsilon_from_sums<N>(sS[w][lane], a.ep);
-            sEps[w][lane] = ep;
-            if (lane < ne) a.eps[k0 + lane] = ep;
-        }
-    } else {
-        if (lane < AV_EPW) sEps[w][lane] = lane < ne ? a.eps[k0 + lane] : 0.0;
     }
     __syncwarp();
-
-    // ---- viscous fluxes of the viscous elements ------------------------------
-    const long long KS = m.KS, KN = m.KN;
-    for (int e = 0; e < ne; ++e) {
-        const double ep = sEps[w][e];
-        const long long k = k0 + e, base = k * nn, side = k * 4 * n;
-        // inviscid elements leave their side-node viscous fluxes unwritten:
-        // the interface average reads only the traces of viscous elements
-        if (!(ep > 0.0)) continue;
-        double* H = Q[e];
-        double* U = sUV[w][0];
-        double* V = sUV[w][1];
+    // ---- the four projections of every element ------------------------
+    // AV_EPW n / 8 tasks per lane, unrolled: the lane's
+    // independent dot products interleave, instead of one dependent chain
+    // of fused multiply-adds at a time
+    static_assert((AV_EPW * P4) % 32 == 0, "projection tasks fill whole warps");
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            if (node < nn) {
-                if (EPS_GIVEN) H[node] = a.W[base + node];
-                U[node] = a.uv[base + node];
-                V[node] = a.uv[KN + base + node];
-            }
+    for (int r = 0; r < AV_EPW * P4 / 32; ++r) {
+        const int s = lane + 32 * r;
+        const int e = s / P4, L = s - e * P4, t = L / n, p = L - t * n;
+        const double* vr = sVi + (t < 2 ? N : N - 1) * n;
+        // t even: sum over i at j = p; t odd: sum over j at i = p. One
+        // code path with an index stride, so that the lanes of a warp do
+        // not split into two half-empty FP64 instruction streams.
+        const int b0 = (t & 1) ? p : p * n, st = (t & 1) ? n : 1;
+        double v = 0.0;
+#pragma unroll
+        for (int q = 0; q < n; ++q) v = fma(vr[q], Q[e][b0 + q * st], v);
+        sP[w][e][L] = v;
+    }
+    // ---- sum w w Q^2: LPE lanes per element ----------------------------
+    const int e4 = lane / LPE, sub = lane % LPE;
+    double swq = 0.0;
+#pragma unroll
+    for (int r = 0; r < (nn + LPE - 1) / LPE; ++r) {
+        const int node = sub + LPE * r;
+        const double q = node < nn ? Q[e4][node] : 0.0;
+        swq = fma(sWW[node < nn ? node : 0] * q, q, swq);
+    }
+#pragma unroll
+    for (int o = 1; o < LPE; o <<= 1) swq += __shfl_xor_sync(0xffffffffu, swq, o);
+    __syncwarp();
+    // ---- the eight projection sums: SPL per lane -----------------------
+    // sum index m: 0..3 weighted squares of y_xi, y_eta, z_xi, z_eta;
+    // 4: B0 = Vinv[N].y_xi, 5: C0 = Vinv[N-1].y_xi, 6: B2 = Vinv[N].z_xi,
+    // 7: C2 = Vinv[N-1].z_xi; each written as sum_p (c_p x_p) y_p
+#pragma unroll
+    for (int h2 = 0; h2 < SPL; ++h2) {
+        const int mi = SPL * sub + h2;
+        const bool sq = mi < 4;
+        const double* x = sP[w][e4] + (sq ? mi : (mi < 6 ? 0 : 2)) * n;
+        const double* c = sVi + ((mi & 1) == 0 ? N : N - 1) * n;
+        double s = 0.0;
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+            const double cp = sq ? c_w[vec_offset(N) + p] : c[p];
+            const double yp = sq ? x[p] : 1.0;
+            s = fma(cp * x[p], yp, s);
         }
-        __syncwarp();
-        // not unrolled: the viscous elements are few, and the unrolled loop
-        // doubled the kernel's registers and halved its occupancy
-#pragma unroll 1
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            if (node >= nn) continue;
-            const int i = node % n, j = node / n;
-            const long long gid = base + node;
+        sS[w][e4][mi] = s;
+    }
+    if (sub == 0) sS[w][e4][8] = swq;
+    __syncwarp();
+    // ---- epsilon, one lane per element --------------------------------
+    if (lane < AV_EPW) {
+        const double ep = epsilon_from_sums<N>(sS[w][lane], a.ep);
+        if (lane < ne) {
+            a.eps[k0 + lane] = ep;
+            if (ep > 0.0) a.vlist[atomicAdd(a.vcount, 1)] = (int)(k0 + lane);
+        }
+    }
+}
+
+// The list of viscous elements from the viscosities already in the work
+// buffer (for a caller that computed them earlier for the same state).
+__global__ void k_visc_list(long long K, const double* __restrict__ eps, int* __restrict__ vlist,
+                            int* __restrict__ vcount) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
+         k += (long long)gridDim.x * blockDim.x)
+        if (eps[k] > 0.0) vlist[atomicAdd(vcount, 1)] = (int)k;
+}
+
+// Elements per block of the viscous-flux kernel (one thread per node, whole
+// elements, about 128 threads) and its block size in whole warps.
+template <int N>
+constexpr int vf_eb() {
+    return (N + 1) * (N + 1) >= 128 ? 1 : 128 / ((N + 1) * (N + 1));
+}
+template <int N>
+constexpr int vf_threads() {
+    return (vf_eb<N>() * (N + 1) * (N + 1) + 31) / 32 * 32;
+}
+
+// Viscous elements only, from the list: the BR1 gradients (strong form with
+// the (U* - u) lift on the outward normal), the viscous fluxes F^v = h eps
+// grad(u), G^v = h eps grad(v), their contravariant forms F~v, G~v, their
+// values at the side nodes for the interface average, and the volume part of
+// the viscous divergence sum_q D_iq F~v_(q,j) + D_jq G~v_(i,q). One thread per
+// node, EB elements per block, the blocks striding over the list; every
+// element's nodes run in parallel, so many viscous elements cost what few do
+// per element (earlier, one warp took its viscous elements one at a time).
+template <int N>
+__global__ void __launch_bounds__(vf_threads<N>()) k_visc_flux(AvArgs a) {
+    constexpr int n = N + 1, nn = n * n, EB = vf_eb<N>();
+    constexpr double iw0 = N * (N + 1) / 2.0;
+    __shared__ double sD[nn];
+    __shared__ double sU[EB][nn], sV[EB][nn];
+    __shared__ double sF[4][EB][nn];
+    if (stopped(a.stop)) return;
+    const DeviceMesh& m = a.m;
+    for (int t = threadIdx.x; t < nn; t += blockDim.x) sD[t] = Dm<N>(t / n, t % n);
+    const int t = threadIdx.x, e = t / nn, node = t - e * nn;
+    const int i = node % n, j = node / n;
+    const long long KS = m.KS, KN = m.KN;
+    const int count = *a.vcount;  // the same for every thread: the loop below is uniform
+    const int groups = (count + EB - 1) / EB;
+    for (int gq = blockIdx.x; gq < groups; gq += gridDim.x) {
+        const int li = gq * EB + e;
+        const bool live = e < EB && li < count;
+        const long long k = live ? a.vlist[li] : 0;
+        const long long base = k * nn, side = k * 4 * n, gid = base + node;
+        const double ep = live ? a.eps[k] : 0.0;
+        if (live) {
+            sU[e][node] = a.uv[gid];
+            sV[e][node] = a.uv[KN + gid];
+        }
+        __syncthreads();  // also: sD, and the previous group's reads of sF done
+        if (live) {
+            const double* U = sU[e];
+            const double* V = sV[e];
             // BR1 gradient: D along xi and eta plus the interface lift
             double ux = 0.0, ue = 0.0, vx = 0.0, ve = 0.0;
 #pragma unroll
@@ -248,7 +270,7 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
             if (j == 0) { const long long sl = side + 0 * n + i; ue -= iw0 * (a.Ustar[sl] - u); ve -= iw0 * (a.Ustar[KS + sl] - v); }
             const double axx = m.axx[gid], axy = m.axy[gid], aex = m.aex[gid], aey = m.aey[gid];
             // J grad u = a_xi du/dxi + a_eta du/deta; F^v = h eps grad(.)
-            const double he = H[node] * ep * m.rJ[gid];
+            const double he = a.W[gid] * ep * m.rJ[gid];
             const double F2 = he * fma(axx, ux, aex * ue);  // h eps U1
             const double G2 = he * fma(axy, ux, aey * ue);  // h eps U2
             const double F3 = he * fma(axx, vx, aex * ve);  // h eps V1
@@ -259,10 +281,10 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
             a.Fvt[KN + gid] = ft3;
             a.Fvt[2 * KN + gid] = gt2;
             a.Fvt[3 * KN + gid] = gt3;
-            sFv[w][0][node] = ft2;
-            sFv[w][1][node] = ft3;
-            sFv[w][2][node] = gt2;
-            sFv[w][3][node] = gt3;
+            sF[0][e][node] = ft2;
+            sF[1][e][node] = ft3;
+            sF[2][e][node] = gt2;
+            sF[3][e][node] = gt3;
             auto put = [&](int f, int p) {
                 const long long sl = side + f * n + p;
                 a.Fvtr[sl] = F2;
@@ -275,43 +297,45 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
             if (j == N) put(2, i);
             if (i == 0) put(3, j);
         }
-        __syncwarp();
-        // volume part of the viscous divergence (the contravariant fluxes of
-        // all the element's nodes are in shared memory now)
-#pragma unroll 1
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            if (node >= nn) continue;
-            const int i = node % n, j = node / n;
+        __syncthreads();
+        if (live) {
             double L2 = 0.0, L3 = 0.0;
 #pragma unroll
             for (int q = 0; q < n; ++q) {
                 const double di = sD[i * n + q], dj = sD[j * n + q];
-                L2 = fma(di, sFv[w][0][j * n + q], L2);
-                L3 = fma(di, sFv[w][1][j * n + q], L3);
-                L2 = fma(dj, sFv[w][2][q * n + i], L2);
-                L3 = fma(dj, sFv[w][3][q * n + i], L3);
+                L2 = fma(di, sF[0][e][j * n + q], L2);
+                L3 = fma(di, sF[1][e][j * n + q], L3);
+                L2 = fma(dj, sF[2][e][q * n + i], L2);
+                L3 = fma(dj, sF[3][e][q * n + i], L3);
             }
-            a.Lv[base + node] = L2;
-            a.Lv[KN + base + node] = L3;
+            a.Lv[gid] = L2;
+            a.Lv[KN + gid] = L3;
         }
-        __syncwarp();
+        __syncthreads();  // sU, sV and sF are rewritten by the next group
     }
 }
 
 template <int N>
 void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s, bool eps_given) {
-    // the wide mapping when it still gives at least 8 warps per SM
-    const bool wide = c->m.K >= (long long)av_epw<N, true>() * 8 * c->sms;
-    const int blocks = grid_for(c->m.K, AV_WPB * (wide ? av_epw<N, true>() : av_epw<N, false>()));
-    Timed tm(c, KC_AV, s);
-    if (wide) {
-        if (eps_given) k_av<N, true, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
-        else k_av<N, false, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+    cudaMemsetAsync(a.vcount, 0, sizeof(int), s);
+    if (!eps_given) {
+        // the wide mapping when it still gives at least 8 warps per SM
+        const bool wide = c->m.K >= (long long)av_epw<N, true>() * 8 * c->sms;
+        const int blocks = grid_for(c->m.K, AV_WPB * (wide ? av_epw<N, true>() : av_epw<N, false>()));
+        Timed tm(c, KC_AV, s);
+        if (wide) k_av<N, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+        else k_av<N, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
     } else {
-        if (eps_given) k_av<N, true, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
-        else k_av<N, false, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+        Timed tm(c, KC_AV, s);
+        k_visc_list<<<grid_for(c->m.K, 256) < 8 * c->sms ? grid_for(c->m.K, 256) : 8 * c->sms, 256, 0, s>>>(
+            c->m.K, a.eps, a.vlist, a.vcount);
     }
+    // blocks striding over the list of viscous elements: at most one group of
+    // EB elements per block per pass, eight blocks per SM
+    const int groups = grid_for(c->m.K, vf_eb<N>());
+    const int blocks = groups < 8 * c->sms ? groups : 8 * c->sms;
+    Timed tm(c, KC_AV, s);
+    k_visc_flux<N><<<blocks, vf_threads<N>(), 0, s>>>(a);
 }
 
 }  // namespace
@@ -323,7 +347,8 @@ EpsParams eps_params(const swe_ctx* c) {
 }
 
 void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given) {
-    AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.Lv, c->w.eps, eps_params(c), stop};
+    AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.Lv, c->w.eps, c->w.vlist, c->w.vcount,
+             eps_params(c), stop};
     switch (c->m.N) {
         case 1: av_n<1>(c, a, s, eps_given); break;
         case 2: av_n<2>(c, a, s, eps_given); break;

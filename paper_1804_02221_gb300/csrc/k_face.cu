@@ -125,6 +125,28 @@ __global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double*
     }
 }
 
+// BR1 interface values alone (U* = {u}, V* = {v} on both sides of every
+// face; the own value at solid walls), for callers that need them without
+// the interface flux (the adjoint's recomputation of the forward quantities).
+__global__ void k_ustar(DeviceMesh m, const double* __restrict__ uv, double* __restrict__ Ustar) {
+    const long long total = (long long)m.nfaces * m.n, walls = (long long)m.nwall * m.n;
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total + walls;
+         t += (long long)gridDim.x * blockDim.x) {
+        if (t < total) {
+            const long long im = m.f_im[t], ip = m.f_ip[t], tm = m.f_tm[t], tp = m.f_tp[t];
+            const double us = 0.5 * (uv[im] + uv[ip]), vs = 0.5 * (uv[m.KN + im] + uv[m.KN + ip]);
+            Ustar[tm] = us;
+            Ustar[m.KS + tm] = vs;
+            Ustar[tp] = us;
+            Ustar[m.KS + tp] = vs;
+        } else {
+            const long long w = t - total, im = m.w_im[w], tm = m.w_tm[w];
+            Ustar[tm] = uv[im];
+            Ustar[m.KS + tm] = uv[m.KN + im];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // BR1 viscous interface flux {F^v . n} (Thm. 1) with the owner's unscaled
 // outward normal; +avg to the owner's slot, -avg to the neighbour's. Only
@@ -132,11 +154,28 @@ __global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double*
 // side's traces count as zero and are not read, and a face between two
 // inviscid elements gets zero without reading any.
 // ---------------------------------------------------------------------------
+//
+// The same launch marks the elements a viscous flux reaches (touch[k] = 1
+// where k or a face neighbour is viscous, else 0), so that the volume kernel
+// skips the viscous lifts of all other elements with one byte per element
+// (the neighbour of face f: the element of the node meeting the face's first
+// node; s_nb < 0 is a wall, which carries no viscous flux).
 __global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, const double* __restrict__ eps,
-                            double* __restrict__ Fvout, const int* stop) {
+                            double* __restrict__ Fvout, uint8_t* __restrict__ touch, const int* stop) {
     if (stopped(stop)) return;
     const long long total = (long long)m.nfaces * m.n;
     const long long S = m.KS, sps = 4LL * m.n;  // side slots per element
+    const long long nn = (long long)m.n * m.n;
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m.K;
+         k += (long long)gridDim.x * blockDim.x) {
+        bool t = nonzero(eps[k]);
+#pragma unroll
+        for (int f = 0; f < 4; ++f) {
+            const long long nb = m.s_nb[k * sps + f * m.n];
+            t |= nb >= 0 && nonzero(eps[nb / nn]);
+        }
+        touch[k] = t ? 1 : 0;
+    }
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long tm = m.f_tm[t], tp = m.f_tp[t];
@@ -709,11 +748,18 @@ void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop
     }
 }
 
+void launch_ustar(swe_ctx* c, cudaStream_t s) {
+    const long long total = ((long long)c->m.nfaces + c->m.nwall) * c->m.n;
+    if (total == 0) return;
+    Timed tm(c, KC_FACE, s);
+    k_ustar<<<grid_for(total, 128), 128, 0, s>>>(c->m, c->w.uv, c->w.Ustar);
+}
+
 void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop) {
     const long long total = (long long)c->m.nfaces * c->m.n;
-    if (total == 0) return;
+    const long long work = total > c->m.K ? total : c->m.K;
     Timed tm(c, KC_VFACE, s);
-    k_visc_face<<<grid_for(total, 128), 128, 0, s>>>(c->m, c->w.Fvtr, c->w.eps, c->w.Fvout, stop);
+    k_visc_face<<<grid_for(work, 128), 128, 0, s>>>(c->m, c->w.Fvtr, c->w.eps, c->w.Fvout, c->w.touch, stop);
 }
 
 void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,

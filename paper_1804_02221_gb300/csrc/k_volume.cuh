@@ -59,6 +59,7 @@ struct VolArgs {
     const double* Fvout;
     const double* Lv;
     const double* eps;
+    const uint8_t* touch;  // 1 where a viscous flux reaches the element (viscous face kernel)
     double* R;
     const int* stop;
 };
@@ -202,6 +203,10 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     const long long side = (valid ? k : 0) * 4 * n;
     const double ek = (AV && valid) ? a.eps[k] : 0.0;
     const bool visc = ek > 0.0;
+    // a viscous interface flux reaches the element only where it or a face
+    // neighbour is viscous; elsewhere the viscous lifts are exactly zero and
+    // are skipped without reading them
+    const bool touch = AV && valid && a.touch[k] != 0;
     double A1[n], A2[n], A3[n], B2[n], B3[n];
 
     // ---- xi-line j = l ----------------------------------------------------
@@ -236,7 +241,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             A1[p] += t1;
             A2[p] = fma(-S(F_U)[nd], t1, fma(wl, a.Fout[KS + sl], A2[p]));
             A3[p] = fma(-S(F_V)[nd], t1, fma(wl, a.Fout[2 * KS + sl], A3[p]));
-            if (AV) {
+            if (AV && touch) {
                 // viscous lift -w_l (F^v*_out - own outward flux); skipped
                 // where no viscous flux reaches the face (both sides inviscid)
                 const double fv2 = a.Fvout[sl], fv3 = a.Fvout[KS + sl];
@@ -305,7 +310,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         };
         if (j == 0) lift(0, i, wi);
         if (j == N) lift(2, i, wi);
-        if (AV) {
+        if (AV && touch) {
             if (visc) {
                 // the volume part of the viscous divergence (AV kernel)
                 const double wij = wi * wq<N>(j);
@@ -335,9 +340,11 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     }
 }
 
-// Small degrees (N <= 2): one thread per element. With 4 or 9 nodes an
-// element's line holds one or three pairs, too little work between the line
-// kernel's staging and hand-over barriers to keep the FP64 pipe busy. Here a
+// N = 1: one thread per element. With 4 nodes an element's line holds one
+// pair, too little work between the line kernel's staging and hand-over
+// barriers to keep the FP64 pipe busy (measured: 7% faster than the line
+// kernel at N = 1; at N = 2, with three pairs a line and 166 registers, 5%
+// slower, so N >= 2 keeps the line kernel). Here a
 // thread holds its whole element in registers (state, velocities, the three
 // accumulators), runs the pairs of all its xi- and eta-lines back to back,
 // then adds the own-velocity parts, the interface lifts (tangential weight
@@ -347,7 +354,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
 // is the launch shape, with the same instructions for every shape.
 template <int N>
 constexpr bool vol_ept() {
-    return N <= 2;
+    return N <= 1;
 }
 
 template <int N>
@@ -423,8 +430,8 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
             A3[d] = fma(wt, a.Fout[2 * m.KS + sl], A3[d]);
         }
     }
-    if (AV) {
-        const bool visc = a.eps[k] > 0.0;
+    const bool visc = AV && a.eps[k] > 0.0;
+    if (AV && a.touch[k] != 0) {
         if (visc) {
             // the volume part of the viscous divergence (AV kernel)
 #pragma unroll
@@ -521,7 +528,7 @@ bool prepare_shape(int N) {
 
 template <int TPB>
 bool launch_shape(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop) {
-    VolArgs a{c->m, W, c->w.uv, c->w.Fout, c->w.Fvt, c->w.Fvout, c->w.Lv, c->w.eps, R, stop};
+    VolArgs a{c->m, W, c->w.uv, c->w.Fout, c->w.Fvt, c->w.Fvout, c->w.Lv, c->w.eps, c->w.touch, R, stop};
     const bool av = c->p.av != 0;
 #define SWE_VOL_CASE(NN) \
     case NN: return av ? launch_n<NN, true, TPB>(c, a, s) : launch_n<NN, false, TPB>(c, a, s);

@@ -64,7 +64,8 @@ enum KernelClass {
     KC_DT = 6,
     KC_REDUCE = 7,
     KC_ADJ = 8,
-    KC_COUNT = 9
+    KC_ADJ_VOL = 9,  // the adjoint of the volume kernel (the other adjoint kernels: KC_ADJ)
+    KC_COUNT = 10
 };
 
 // Device-side data of one context. Nodal arrays are [K][n][n] planes,
@@ -134,6 +135,9 @@ struct Work {
     double* Fvout;  // [2][KS] outward viscous interface flux
     double* Lv;     // [2][KN] volume part of the viscous divergence, sum_q D_iq F~v + D_jq G~v
                     // (components 2, 3; written and read for viscous elements only)
+    uint8_t* touch; // [K] 1 where the element or a face neighbour is viscous (viscous face kernel)
+    int* vlist;     // [K] viscous elements (AV indicator), vcount of them
+    int* vcount;
     double* eps;    // [K]
     double* Kreg;   // [3][KN] 2N-storage register
     double* Wn;     // [3][KN] state at the start of a step
@@ -233,6 +237,7 @@ EpsParams eps_params(const swe_ctx* c);
 // eps_given: the element viscosities of W are already in the work buffer
 void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given);
 void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop);
+void launch_ustar(swe_ctx* c, cudaStream_t s);
 // mode 0: limiter only; 1: 2N-storage stage Kh = a Kh + R, W += (b dt) Kh
 // (the register holds K/dt); 2: SSP stage W = a Wn + b (W + dt R).
 // write_uv: also write the velocities of the new state into the work buffer.

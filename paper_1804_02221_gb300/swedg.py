@@ -17,7 +17,7 @@ from . import build as _build
 
 OK, ERR_ARG, ERR_GEOM, ERR_NEG_MEAN, ERR_NONFINITE, ERR_CUDA = 0, -1, -2, -3, -4, -5
 KERNEL_CLASSES = {"volume": 0, "face": 1, "prim": 2, "av": 3, "visc_face": 4, "update": 5, "dt": 6,
-                  "reduce": 7, "adjoint": 8}
+                  "reduce": 7, "adjoint": 8, "adjoint_volume": 9}
 
 SYMBOLS = ["swe_create", "swe_destroy", "swe_rhs", "swe_limit", "swe_max_dt", "swe_step", "swe_mass",
            "swe_entropy", "swe_get_epsilon", "swe_status", "swe_timing", "swe_timing_classes",
