@@ -446,12 +446,11 @@ extern "C" void swe_destroy(swe_ctx* c) {
 
 namespace swe {
 
-void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done,
-               bool eps_done) {
+void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done) {
     if (!prim_done) launch_prim(c, W, s, stop);
     launch_surface(c, W, s, stop);
     if (c->p.av) {
-        launch_av(c, W, s, stop, eps_done);
+        launch_av(c, W, s, stop);
         launch_visc_face(c, s, stop);
     }
     launch_volume(c, W, R, s, stop);
@@ -470,7 +469,7 @@ void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop
     for (int stage = 0; stage < stages; ++stage) {
         if (stage == 0 && visc_dt) {
             launch_surface(c, W, s, stop);
-            launch_av(c, W, s, stop, false);
+            launch_av(c, W, s, stop);
             launch_dt(c, W, 0.0, s, stop);
             launch_visc_face(c, s, stop);
             launch_volume(c, W, c->w.R, s, stop);
@@ -517,7 +516,7 @@ extern "C" int swe_max_dt(swe_ctx* c, const double* W, double* dt_cfl, double* d
     swe::launch_prim(c, W, s, nullptr);
     if (c->kv > 0.0) {  // the element viscosities of W for the viscous restriction
         swe::launch_surface(c, W, s, nullptr);
-        swe::launch_av(c, W, s, nullptr, false);
+        swe::launch_av(c, W, s, nullptr);
     }
     swe::launch_dt(c, W, 0.0, s, nullptr);
     double h[4];
@@ -801,7 +800,7 @@ static void adjoint_prerequisites(swe_ctx* c, const double* W, cudaStream_t s, b
     swe::launch_prim(c, W, s, nullptr);
     if (!c->p.av) return;
     swe::launch_ustar(c, s);
-    if (!eps_given) swe::launch_av(c, W, s, nullptr, false);
+    if (!eps_given) swe::launch_av(c, W, s, nullptr);
 }
 
 extern "C" int swe_rhs_adjoint(swe_ctx* c, const double* W, const double* Rbar, double* Wbar, double* bbar,

@@ -233,7 +233,7 @@ extern "C" int swe_ens_max_dt(swe_ens* e, const double* W, double* dt_cfl, doubl
         swe::launch_prim(c, W + e->goff[gi], s, nullptr);
         if (c->kv > 0.0) {  // the element viscosities for the viscous restriction
             swe::launch_surface(c, W + e->goff[gi], s, nullptr);
-            swe::launch_av(c, W + e->goff[gi], s, nullptr, false);
+            swe::launch_av(c, W + e->goff[gi], s, nullptr);
         }
         swe::launch_dt(c, W + e->goff[gi], 0.0, s, nullptr);
     }

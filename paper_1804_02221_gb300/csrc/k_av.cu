@@ -196,15 +196,6 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
     }
 }
 
-// The list of viscous elements from the viscosities already in the work
-// buffer (for a caller that computed them earlier for the same state).
-__global__ void k_visc_list(long long K, const double* __restrict__ eps, int* __restrict__ vlist,
-                            int* __restrict__ vcount) {
-    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
-         k += (long long)gridDim.x * blockDim.x)
-        if (eps[k] > 0.0) vlist[atomicAdd(vcount, 1)] = (int)k;
-}
-
 // Elements per block of the viscous-flux kernel (one thread per node, whole
 // elements, about 128 threads) and its block size in whole warps.
 template <int N>
@@ -316,19 +307,15 @@ __global__ void __launch_bounds__(vf_threads<N>()) k_visc_flux(AvArgs a) {
 }
 
 template <int N>
-void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s, bool eps_given) {
+void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s) {
     cudaMemsetAsync(a.vcount, 0, sizeof(int), s);
-    if (!eps_given) {
+    {
         // the wide mapping when it still gives at least 8 warps per SM
         const bool wide = c->m.K >= (long long)av_epw<N, true>() * 8 * c->sms;
         const int blocks = grid_for(c->m.K, AV_WPB * (wide ? av_epw<N, true>() : av_epw<N, false>()));
         Timed tm(c, KC_AV, s);
         if (wide) k_av<N, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
         else k_av<N, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
-    } else {
-        Timed tm(c, KC_AV, s);
-        k_visc_list<<<grid_for(c->m.K, 256) < 8 * c->sms ? grid_for(c->m.K, 256) : 8 * c->sms, 256, 0, s>>>(
-            c->m.K, a.eps, a.vlist, a.vcount);
     }
     // blocks striding over the list of viscous elements: at most one group of
     // EB elements per block per pass, eight blocks per SM
@@ -346,22 +333,22 @@ EpsParams eps_params(const swe_ctx* c) {
     return EpsParams{c->p.eps0, c->sigma_min, c->sigma_max, pow(10.0, c->sigma_min), pow(10.0, c->sigma_max)};
 }
 
-void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given) {
+void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
     AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.Lv, c->w.eps, c->w.vlist, c->w.vcount,
              eps_params(c), stop};
     switch (c->m.N) {
-        case 1: av_n<1>(c, a, s, eps_given); break;
-        case 2: av_n<2>(c, a, s, eps_given); break;
-        case 3: av_n<3>(c, a, s, eps_given); break;
-        case 4: av_n<4>(c, a, s, eps_given); break;
-        case 5: av_n<5>(c, a, s, eps_given); break;
-        case 6: av_n<6>(c, a, s, eps_given); break;
-        case 7: av_n<7>(c, a, s, eps_given); break;
-        case 8: av_n<8>(c, a, s, eps_given); break;
-        case 9: av_n<9>(c, a, s, eps_given); break;
-        case 10: av_n<10>(c, a, s, eps_given); break;
-        case 11: av_n<11>(c, a, s, eps_given); break;
-        case 12: av_n<12>(c, a, s, eps_given); break;
+        case 1: av_n<1>(c, a, s); break;
+        case 2: av_n<2>(c, a, s); break;
+        case 3: av_n<3>(c, a, s); break;
+        case 4: av_n<4>(c, a, s); break;
+        case 5: av_n<5>(c, a, s); break;
+        case 6: av_n<6>(c, a, s); break;
+        case 7: av_n<7>(c, a, s); break;
+        case 8: av_n<8>(c, a, s); break;
+        case 9: av_n<9>(c, a, s); break;
+        case 10: av_n<10>(c, a, s); break;
+        case 11: av_n<11>(c, a, s); break;
+        case 12: av_n<12>(c, a, s); break;
         default: break;
     }
 }

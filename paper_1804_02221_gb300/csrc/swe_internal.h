@@ -234,8 +234,9 @@ void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop
 void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
 void launch_volume_std(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
 EpsParams eps_params(const swe_ctx* c);
-// eps_given: the element viscosities of W are already in the work buffer
-void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool eps_given);
+// The element viscosities of W (indicator), and for the viscous elements the
+// BR1 gradients, viscous fluxes and the volume part of their divergence.
+void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop);
 void launch_ustar(swe_ctx* c, cudaStream_t s);
 // mode 0: limiter only; 1: 2N-storage stage Kh = a Kh + R, W += (b dt) Kh
@@ -263,10 +264,8 @@ void launch_reduce_inst(swe_ctx* c, const double* W, const long long* ebeg, doub
 void launch_rate(swe_ctx* c, const double* W, const double* R, double* host_out, cudaStream_t s);
 
 // One right-hand side R(W) (prim_done: the velocities of W are already in
-// the work buffer, written by the previous stage update; eps_done: so are its
-// element viscosities).
-void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done,
-               bool eps_done = false);
+// the work buffer, written by the previous stage update).
+void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done);
 // One Runge-Kutta step of W (dt <= 0: adaptive, from the device time step of
 // every instance). Expects the velocities of W in the work buffer and leaves
 // those of the new state there. save: first copy the start state to w.Wn

@@ -333,6 +333,23 @@ def test_rhs_full_size_dam_break_N7():
     assert np.abs(g.epsilon().cpu().numpy() - eo).max() < 1e-12
 
 
+@pytest.mark.parametrize("N", [1, 7])
+def test_rhs_full_size_every_element_viscous(N):
+    """The degree-sweep workload with the indicator thresholds set so that
+    every element carries eps0: the viscous fluxes of all elements (the list
+    of viscous elements, many groups per block of the viscous-flux kernel),
+    every element's viscous lifts and divergence, against the oracle."""
+    K1 = int(round(2048 / (N + 1)))
+    p = I.dam_break(N=N, K1=K1)
+    kw = dict(flux=1, av=True, eps0=0.025, sigma_min=-301.0, sigma_max=-300.0)
+    o, g = pair(p, **kw)
+    Ro = o.rhs(p.W)
+    Rg = g.rhs(dev(p.W)).cpu().numpy()
+    assert np.all(o.epsilon() == kw["eps0"])
+    assert np.array_equal(g.epsilon().cpu().numpy(), o.epsilon())
+    check_rhs(Rg, Ro, p)
+
+
 @pytest.mark.parametrize("N", [1, 3, 12])
 def test_rhs_full_size_degree_sweep(N):
     """The degree sweep's workloads (~4.2M nodes: K1 = round(2048/(N+1))
