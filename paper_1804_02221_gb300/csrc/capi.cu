@@ -793,14 +793,15 @@ int adjoint_args(swe_ctx* c, const void* W, const void* cot, const void* Wbar, c
 }  // namespace
 
 // The forward quantities the reverse sweep reads at W: velocities and, with
-// the viscosity on, the BR1 interface values and (unless given) the element
-// viscosities with the BR1 gradients. The interface flux, the volume term
+// the viscosity on, the BR1 interface values, the element viscosities (unless
+// given) and the list of viscous elements. The interface flux, the volume term
 // and the viscous interface average themselves are not needed.
 static void adjoint_prerequisites(swe_ctx* c, const double* W, cudaStream_t s, bool eps_given) {
     swe::launch_prim(c, W, s, nullptr);
     if (!c->p.av) return;
     swe::launch_ustar(c, s);
     if (!eps_given) swe::launch_av(c, W, s, nullptr);
+    else swe::launch_visc_list(c, s);  // the list of the recorded viscosities
 }
 
 extern "C" int swe_rhs_adjoint(swe_ctx* c, const double* W, const double* Rbar, double* Wbar, double* bbar,

@@ -330,8 +330,11 @@ __global__ void k_visc_face_adj(DeviceMesh m, const double* __restrict__ Gfvo, d
 }
 
 // ---------------------------------------------------------------------------
-// BR1 and the viscous fluxes in reverse, one warp per element. Non-viscous
-// elements only zero their BR1 interface-value cotangents.
+// BR1 and the viscous fluxes in reverse, one warp per viscous element: the
+// warps of a fixed grid stride over the list of viscous elements (built with
+// the forward quantities). The BR1 interface-value cotangents of the other
+// elements are zero (cleared before the launch), and a viscous element
+// writes all of its side slots.
 // ---------------------------------------------------------------------------
 constexpr int AVA_WPB = 4;
 
@@ -346,6 +349,8 @@ struct AvAdjArgs {
     double* Ga;    // += h cotangent
     double* Guv;   // += (u, v) cotangents
     double* GUs;   // [2][KS] out: cotangents of the BR1 interface values
+    const int* vlist;   // the viscous elements, vcount of them
+    const int* vcount;
 };
 
 template <int N>
@@ -359,16 +364,11 @@ __global__ void __launch_bounds__(32 * AVA_WPB) k_av_adj(AvAdjArgs a) {
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long KN = m.KN, KS = m.KS;
     constexpr double iw0 = N * (N + 1) / 2.0;
-    for (long long k = (long long)blockIdx.x * AVA_WPB + w; k < m.K; k += (long long)gridDim.x * AVA_WPB) {
+    const int count = *a.vcount;
+    for (int li = blockIdx.x * AVA_WPB + w; li < count; li += gridDim.x * AVA_WPB) {
+        const long long k = a.vlist[li];
         const double ep = a.eps[k];
         const long long base = k * nn, side = k * 4 * n;
-        if (!(ep > 0.0)) {
-            for (int s = lane; s < 4 * n; s += 32) {
-                a.GUs[side + s] = 0.0;
-                a.GUs[KS + side + s] = 0.0;
-            }
-            continue;
-        }
         double ubar[PER], vbar[PER];
 #pragma unroll
         for (int r = 0; r < PER; ++r) {
@@ -628,8 +628,10 @@ struct GatherArgs {
     double* bbar;  // nullable
 };
 
+// Five blocks per SM (at most 102 registers; 164 without the bound, three
+// blocks): the per-node gathers are latency-bound and want the warps.
 template <int N>
-__global__ void __launch_bounds__(32 * GA_WPB) k_gather_adj(GatherArgs a) {
+__global__ void __launch_bounds__(32 * GA_WPB, 5) k_gather_adj(GatherArgs a) {
     constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
     __shared__ double sD[nn];
     __shared__ double sC[GA_WPB][4][nn];  // cx, cy, axx cx + axy cy, aex cx + aey cy
@@ -713,7 +715,7 @@ __global__ void __launch_bounds__(32 * GA_WPB) k_gather_adj(GatherArgs a) {
 // source-coefficient cotangents summed over several stages (the map is
 // linear and depends on the geometry only). One warp per element.
 template <int N>
-__global__ void __launch_bounds__(32 * GA_WPB) k_src_adj(DeviceMesh m, const double* __restrict__ Gsrc,
+__global__ void __launch_bounds__(32 * GA_WPB, 5) k_src_adj(DeviceMesh m, const double* __restrict__ Gsrc,
                                                          double* __restrict__ bbar) {
     constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
     __shared__ double sD[nn];
@@ -1077,11 +1079,15 @@ void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* W
             Timed tm(c, KC_ADJ, s);
             k_visc_face_adj<<<grid_for(total, 128), 128, 0, s>>>(m, A.Gfvo, A.Gfvtr);
         }
-        AvAdjArgs aa{m, W, c->w.uv, c->w.Ustar, c->w.eps, A.Gfvt, A.Gfvtr, A.Ga, A.Guv, A.GUs};
+        AvAdjArgs aa{m, W, c->w.uv, c->w.Ustar, c->w.eps, A.Gfvt, A.Gfvtr, A.Ga, A.Guv, A.GUs,
+                     c->w.vlist, c->w.vcount};
+        cudaMemsetAsync(A.GUs, 0, sizeof(double) * 2 * (size_t)m.KS, s);
+        // a fixed grid striding over the list: sixteen blocks per SM at most
+        const int ablocks = grid_for(m.K, AVA_WPB) < 16 * c->sms ? grid_for(m.K, AVA_WPB) : 16 * c->sms;
 #define SWE_AA(NN)                                                                         \
     {                                                                                      \
         Timed tm(c, KC_ADJ, s);                                                            \
-        k_av_adj<NN><<<grid_for(m.K, AVA_WPB), 32 * AVA_WPB, 0, s>>>(aa);                  \
+        k_av_adj<NN><<<ablocks, 32 * AVA_WPB, 0, s>>>(aa);                                 \
     }
         SWE_SWITCH_N_ADJ(m.N, SWE_AA)
 #undef SWE_AA

@@ -196,6 +196,15 @@ __global__ void __launch_bounds__(32 * AV_WPB) k_av(AvArgs a) {
     }
 }
 
+// The list of viscous elements from the viscosities already in the work
+// buffer (the adjoint sweeps set them from the forward pass's records).
+__global__ void k_visc_list(long long K, const double* __restrict__ eps, int* __restrict__ vlist,
+                            int* __restrict__ vcount) {
+    for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < K;
+         k += (long long)gridDim.x * blockDim.x)
+        if (eps[k] > 0.0) vlist[atomicAdd(vcount, 1)] = (int)k;
+}
+
 // Elements per block of the viscous-flux kernel (one thread per node, whole
 // elements, about 128 threads) and its block size in whole warps.
 template <int N>
@@ -328,6 +337,13 @@ void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s) {
 }  // namespace
 
 void init_tables_av() { upload_tables(); }
+
+void launch_visc_list(swe_ctx* c, cudaStream_t s) {
+    cudaMemsetAsync(c->w.vcount, 0, sizeof(int), s);
+    const int blocks = grid_for(c->m.K, 256) < 8 * c->sms ? grid_for(c->m.K, 256) : 8 * c->sms;
+    Timed tm(c, KC_AV, s);
+    k_visc_list<<<blocks, 256, 0, s>>>(c->m.K, c->w.eps, c->w.vlist, c->w.vcount);
+}
 
 EpsParams eps_params(const swe_ctx* c) {
     return EpsParams{c->p.eps0, c->sigma_min, c->sigma_max, pow(10.0, c->sigma_min), pow(10.0, c->sigma_max)};

@@ -237,6 +237,8 @@ EpsParams eps_params(const swe_ctx* c);
 // The element viscosities of W (indicator), and for the viscous elements the
 // BR1 gradients, viscous fluxes and the volume part of their divergence.
 void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+// The list of viscous elements (w.vlist, w.vcount) from the viscosities in w.eps.
+void launch_visc_list(swe_ctx* c, cudaStream_t s);
 void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop);
 void launch_ustar(swe_ctx* c, cudaStream_t s);
 // mode 0: limiter only; 1: 2N-storage stage Kh = a Kh + R, W += (b dt) Kh
