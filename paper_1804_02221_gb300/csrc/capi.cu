@@ -233,6 +233,8 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     // (the standard volume form has no pairs)
     std::vector<double> pm(p->volume == 1 ? 0 : (size_t)K * 2 * NP * 2 * n), fwJ(KN);
     for (long long a = 0; a < KN; ++a) fwJ[a] = -1.0 / wJ[a];
+    std::vector<double> fwJ2(p->volume == 1 ? 0 : KN);
+    for (size_t a = 0; a < fwJ2.size(); ++a) fwJ2[a] = 2.0 * fwJ[a];  // exact
     for (int k = 0; k < K && p->volume == 0; ++k)
         for (int d = 0; d < 2; ++d) {
             const double* vx = d == 0 ? axx.data() : aex.data();
@@ -355,7 +357,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: upload"); }
     UP(m.axx, axx) UP(m.axy, axy) UP(m.aex, aex) UP(m.aey, aey) UP(m.rJ, rJ) UP(m.wJ, wJ)
     UP(m.srcx, srcx) UP(m.srcy, srcy) UP(m.bn, bn) UP(m.nax, cfln) UP(m.rvol, rvol)
-    UP(m.fwJ, fwJ) UP(m.pm, pm)
+    UP(m.fwJ, fwJ) UP(m.fwJ2, fwJ2) UP(m.pm, pm)
     UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
     UP(m.f_ny, f_ny) UP(m.f_js, f_js) UP(m.f_sx, f_sx) UP(m.f_sy, f_sy) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
     UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)

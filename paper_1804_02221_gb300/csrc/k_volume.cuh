@@ -22,7 +22,8 @@
 //    formed per pair: each node accumulates A1 = sum of +-Q and, per pair,
 //    only the partner's velocity term, u_q Q + P Sx at node i and
 //    -(u_i Q + P Sx) at node q; after both lines the node adds u A1 (and
-//    v A1) and doubles A1. One pair is then 15 FP64 instructions (4 for Q,
+//    v A1), and the mass row 2 A1 is scaled by 2f = -2/(w_i w_j J) instead
+//    of doubling A1. One pair is then 15 FP64 instructions (4 for Q,
 //    1 for P, 2 for the mass sums, 8 fused multiply-adds for the momenta).
 //    From N = 5 up the pressure parts P Sx = p_i (h_q Sx) are summed per
 //    node as h_q Sx (B2, B3) and scaled by the node's p = 2g h once per line:
@@ -281,20 +282,22 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             }
         }
     }
-    // own-velocity parts of the momentum fluxes, then the mass flux 2 sum Q
+    // own-velocity parts of the momentum fluxes; A1 keeps sum Q (half the
+    // mass flux difference): the mass row is scaled by 2f = -2/(w_i w_j J) at
+    // the end and its remaining lifts take half weights, which gives f (2 A1 +
+    // w F) bit for bit without forming 2 A1
 #pragma unroll
     for (int p = 0; p < n; ++p) {
         const int nd = e * nn + p * n + l;
         A2[p] = fma(S(F_U)[nd], A1[p], A2[p]);
         A3[p] = fma(S(F_V)[nd], A1[p], A3[p]);
-        A1[p] += A1[p];
     }
 
     if (!valid) return;
 
     // ---- nodes (i = l, j = p): lifts, viscous terms, source, scaling --------
     const int i = l;
-    const double wi = wq<N>(i);
+    const double wi = wq<N>(i), wih = 0.5 * wi;
     const int eb = e * nn;
 #pragma unroll
     for (int p = 0; p < n; ++p) {
@@ -302,14 +305,15 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         const long long gid = k * nn + j * n + i;
         double a1 = A1[p], a2 = A2[p], a3 = A3[p];
         // interface flux: w_i w_j (1/w_0) F_out = (tangential weight) F_out
-        auto lift = [&](int f, int pn, double wt) {
+        // (half of it in the mass row, which is scaled by 2f)
+        auto lift = [&](int f, int pn) {
             const long long sl = side + f * n + pn;
-            a1 = fma(wt, a.Fout[sl], a1);
-            a2 = fma(wt, a.Fout[KS + sl], a2);
-            a3 = fma(wt, a.Fout[2 * KS + sl], a3);
+            a1 = fma(wih, a.Fout[sl], a1);
+            a2 = fma(wi, a.Fout[KS + sl], a2);
+            a3 = fma(wi, a.Fout[2 * KS + sl], a3);
         };
-        if (j == 0) lift(0, i, wi);
-        if (j == N) lift(2, i, wi);
+        if (j == 0) lift(0, i);
+        if (j == N) lift(2, i);
         if (AV && touch) {
             if (visc) {
                 // the volume part of the viscous divergence (AV kernel)
@@ -334,7 +338,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         }
         const double f = m.fwJ[gid];
         const double h = S(F_H)[eb + j * n + i];
-        a.R[gid] = f * a1;
+        a.R[gid] = m.fwJ2[gid] * a1;
         a.R[m.KN + gid] = fma(h, m.srcx[gid], f * a2);
         a.R[2 * m.KN + gid] = fma(h, m.srcy[gid], f * a3);
     }

@@ -91,6 +91,7 @@ struct DeviceMesh {
     const double* nae;  // |a_eta| / J
     const double* rvol; // [K] 1 / sum_ij w_i w_j J
     const double* fwJ;  // -1 / (w_i w_j J)
+    const double* fwJ2; // -2 / (w_i w_j J) (the split volume kernel's mass row; empty otherwise)
     // Pair constants of the volume kernel, [K][2 directions][N(N+1)/2 pairs][n lines][2]:
     // w_i w_j D_iq / 4 * (a_i + a_q) for the pair (i, q), i < q, of each line; the
     // two components of a line are adjacent (one 16-byte load).
