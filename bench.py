@@ -135,11 +135,11 @@ def volume_flops_per_node(N):
 
 def volume_bytes_per_node(N):
     """Compulsory DRAM bytes: W (24), velocities (16), per-pair metric
-    constants (2 doubles per pair, N pairs per node: 16N), -1/(w w J) (8),
-    source coefficients (16), R (24), interface flux traces 3 x 4(N+1) doubles
-    per element."""
+    constants (2 doubles per pair, N pairs per node: 16N), -1/(w w J) and
+    -2/(w w J) (16), source coefficients (16), R (24), interface flux traces
+    3 x 4(N+1) doubles per element."""
     n = N + 1
-    return 88 + 16 * N + 3 * 8 * 4 * n / (n * n)
+    return 96 + 16 * N + 3 * 8 * 4 * n / (n * n)
 
 
 def volume_traffic(N, nodes):
