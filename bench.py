@@ -57,6 +57,13 @@ def parse():
     ap.add_argument("--adjoint", action="store_true",
                     help="gauge-misfit gradient by the adjoint (N=4, 64x64 quads, 200 steps, 64 gauges, "
                          "checkpoints every 20 steps): one JSON line against the plain forward path")
+    ap.add_argument("--case", default=None, choices=["rhs", "step", "ensemble", "rhs_adjoint"],
+                    help="one small, untimed invocation for profiler captures (no JSON line): "
+                         "rhs = --reps right-hand sides of the ES+AV dam break at --N on --K1 x --K1 quads; "
+                         "step = one warm-up step and one step with its integrals (every kernel class); "
+                         "ensemble = one warm-up step (graph capture) and --steps steps of the 256-member "
+                         "ensemble; rhs_adjoint = --reps right-hand-side adjoints of the dam break")
+    ap.add_argument("--reps", type=int, default=3, help="repetitions of a --case invocation")
     ap.add_argument("--sweep", default=None,
                     help="comma-separated degrees: one JSON line per degree at ~4.2M nodes "
                          "(step rate, right-hand-side rates, volume-kernel roofline)")
@@ -703,8 +710,59 @@ def developed_leg(prob, W0, args, shapes, barrier, advance=200, cfl_visc=0.25, a
     return out
 
 
+def profile_case(args):
+    """Small invocations that ncu captures; they print a check value, not a rate."""
+    import torch
+
+    from paper_1804_02221_gb300 import inputs as I
+    from paper_1804_02221_gb300 import swedg
+
+    torch.cuda.set_device(0)
+    if args.case == "ensemble":
+        probs = I.ensemble(256)
+        ens = swedg.SweEnsemble(probs, flux=1, av=True, eps0=0.01, limiter=True, rk=0, cfl=0.5)
+        W = ens.pack([p.W for p in probs])
+        ens.step(W, 0.0, 1)
+        ens.step(W, 0.0, args.steps)
+        torch.cuda.synchronize()
+        print("ok", float(W.abs().max()), "kernels per step", ens.launches())
+        ens.close()
+        return
+    N = args.N
+    K1 = args.K1 or int(round(2048 / (N + 1)))
+    p = I.dam_break(N=N, K1=K1)
+    if args.case == "step":
+        ctx = swedg.SweContext.from_problem(p, flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
+    else:
+        ctx = swedg.SweContext.from_problem(p, flux=1, av=True, eps0=0.025)
+    W0 = torch.from_numpy(p.W).cuda()
+    if args.case == "rhs":
+        R = torch.empty_like(W0)
+        for _ in range(args.reps):
+            ctx.rhs(W0, R)
+        check = float(R.abs().max())
+    elif args.case == "step":
+        W = W0.clone()
+        ctx.step(W, 0.0, 1)
+        W.copy_(W0)
+        check = ctx.step_integrals(W, 0.0, 1)
+    else:
+        gen = torch.Generator(device="cuda").manual_seed(1)
+        Rb = torch.randn(W0.shape, dtype=W0.dtype, device="cuda", generator=gen)
+        Wb, bb = torch.zeros_like(W0), torch.zeros_like(W0[0])
+        for _ in range(args.reps):
+            ctx.rhs_adjoint(W0, Rb, Wb, bb)
+        check = float(Wb.abs().max())
+    torch.cuda.synchronize()
+    print("ok", check)
+    ctx.close()
+
+
 def main():
     args = parse()
+    if args.case:
+        profile_case(args)
+        return
     if args.impl == "reference":
         run_reference(args)
         return
