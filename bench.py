@@ -725,7 +725,7 @@ def profile_case(args):
         ens.step(W, 0.0, 1)
         ens.step(W, 0.0, args.steps)
         torch.cuda.synchronize()
-        print("ok", float(W.abs().max()), "kernels per step", ens.launches())
+        print("ok", float(W.abs().max()), "launches", ens.launches())
         ens.close()
         return
     N = args.N

@@ -53,8 +53,11 @@ __host__ __device__ constexpr int pair_index_adj(int i, int q) {
 //   Q^ = 2 d1 + (u_i + u_q) d2 + (v_i + v_q) d3,  P^ = 2g (S_x d2 + S_y d3),
 //   u^_{i,q} += Q d2, v^_{i,q} += Q d3, hu^_{i,q} += S_x Q^, hv^_{i,q} += S_y Q^,
 //   h^_i += h_q P^, h^_q += h_i P^.
+// Q^ is formed from the per-node theta = 2 A^1 + u A^2 + v A^3 (staged in
+// place of A^1): Q^ = theta_i - theta_q + u_q A^2_i - u_i A^2_q
+// + v_q A^3_i - v_i A^3_q, which needs neither d1 nor the velocity sums.
 // The factor 2g of P^ is applied once per node after both lines (gH holds
-// h^ / 2g), and every cotangent sum is a fused multiply-add: 24 FP64
+// h^ / 2g), and every cotangent sum is a fused multiply-add: 23 FP64
 // instructions per pair.
 template <int N, int BLK>
 __device__ __forceinline__ void pair_loop_adj(const double* __restrict__ s, int base, int stride,
@@ -73,16 +76,18 @@ __device__ __forceinline__ void pair_loop_adj(const double* __restrict__ s, int 
     for (int i = 0; i < n; ++i) {
         const int ni = base + i * stride;
         const double h_i = sH[ni], hu_i = sHU[ni], hv_i = sHV[ni], u_i = sU[ni], v_i = sV[ni];
-        const double a1 = sA1[ni], a2 = sA2[ni], a3 = sA3[ni];
+        const double th_i = sA1[ni], a2 = sA2[ni], a3 = sA3[ni];
 #pragma unroll
         for (int q = i + 1; q < n; ++q) {
             const int nq = base + q * stride;
             const int pr = pair_index_adj<N>(i, q);
             const double2 c = __ldg(reinterpret_cast<const double2*>(pmk + 2 * pr * n));
             const double sx = c.x, sy = c.y;
-            const double d1 = a1 - sA1[nq], d2 = a2 - sA2[nq], d3 = a3 - sA3[nq];
+            const double a2q = sA2[nq], a3q = sA3[nq];
+            const double d2 = a2 - a2q, d3 = a3 - a3q;
             const double Q = fma(hu_i + sHU[nq], sx, (hv_i + sHV[nq]) * sy);
-            const double Qb = fma(v_i + sV[nq], d3, fma(u_i + sU[nq], d2, 2.0 * d1));
+            const double Qb =
+                fma(-v_i, a3q, fma(sV[nq], a3, fma(-u_i, a2q, fma(sU[nq], a2, th_i - sA1[nq]))));
             const double Pb = fma(sy, d3, sx * d2);
             gU[i] = fma(Q, d2, gU[i]);
             gU[q] = fma(Q, d2, gU[q]);
@@ -147,7 +152,7 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
         S(F_HV)[idx] = hv;
         S(F_U)[idx] = u;
         S(F_V)[idx] = v;
-        S(F_A1)[idx] = b1;
+        S(F_A1)[idx] = fma(v, b3, fma(u, b2, 2.0 * b1));  // theta
         S(F_A2)[idx] = b2;
         S(F_A3)[idx] = b3;
     }
@@ -214,12 +219,12 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
             a.Gsrc[gid] = h * rb2;
             a.Gsrc[KN + gid] = h * rb3;
         }
-        const double b1 = S(F_A1)[eb + j * n + i], b2 = S(F_A2)[eb + j * n + i], b3 = S(F_A3)[eb + j * n + i];
+        const double b2 = S(F_A2)[eb + j * n + i], b3 = S(F_A3)[eb + j * n + i];
         // a_c += wt F_out,c  =>  F_out^ = wt a^_c;  a_c -= wt (Fv_out - own)  =>  Fv_out^ = -wt a^_c
         // (every element takes the viscous interface flux, viscous or not)
         auto lift = [&](int f, int pn, double wt) {
             const long long sl = side + f * n + pn;
-            a.Gfo[sl] = wt * b1;
+            a.Gfo[sl] = wt * (m.fwJ[gid] * a.Rb[gid]);  // A^1 (the plane holds theta)
             a.Gfo[KS + sl] = wt * b2;
             a.Gfo[2 * KS + sl] = wt * b3;
             if (AV) {
@@ -238,7 +243,8 @@ __global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_volume_adj(VolAdjArgs
         for (int end = 0; end < 2; ++end) {
             const int pi = end == 0 ? N : 0, f = end == 0 ? 1 : 3;
             const int nd = eb + l * n + pi;
-            const double b1 = S(F_A1)[nd], b2 = S(F_A2)[nd], b3 = S(F_A3)[nd];
+            const long long gnd = k * nn + l * n + pi;
+            const double b1 = m.fwJ[gnd] * a.Rb[gnd], b2 = S(F_A2)[nd], b3 = S(F_A3)[nd];
             const long long sl = side + f * n + l;
             a.Gfo[sl] = wl * b1;
             a.Gfo[KS + sl] = wl * b2;
@@ -609,12 +615,13 @@ __global__ void k_wall_adj(DeviceMesh m, const double* __restrict__ W, const dou
 }
 
 // ---------------------------------------------------------------------------
-// Gather: slot cotangents onto nodes, u = hu/h in reverse, and the source
-// coefficients' cotangents onto b (srcx = -(g/2) gx/J with
-// gx = axx D_xi b + D_xi(axx b) + aex D_eta b + D_eta(aex b), gy likewise with
-// axy, aey). One warp per element; accumulates into the caller's Wbar, bbar.
+// Gather: slot cotangents onto nodes and u = hu/h in reverse; the slot
+// cotangents of b (the interface fluxes' bathymetry jumps) go to bbar.
+// One thread per node (a streaming kernel: full occupancy hides the
+// latency of its dozen independent loads); accumulates into the caller's
+// Wbar, bbar. The source coefficients' part of bbar is k_src_adj's.
 // ---------------------------------------------------------------------------
-constexpr int GA_WPB = 4;
+constexpr int GA_TPB = 256;
 
 struct GatherArgs {
     DeviceMesh m;
@@ -623,142 +630,145 @@ struct GatherArgs {
     const double* Ga;
     const double* Guv;
     const double* Gsl;
-    const double* Gsrc;  // nullable: the source part is deferred (k_src_adj)
     double* Wbar;
     double* bbar;  // nullable
 };
 
-// Five blocks per SM (at most 102 registers; 164 without the bound, three
-// blocks): the per-node gathers are latency-bound and want the warps.
 template <int N>
-__global__ void __launch_bounds__(32 * GA_WPB, 5) k_gather_adj(GatherArgs a) {
-    constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
-    __shared__ double sD[nn];
-    __shared__ double sC[GA_WPB][4][nn];  // cx, cy, axx cx + axy cy, aex cx + aey cy
-    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) sD[idx] = Dm<N>(idx / n, idx % n);
-    __syncthreads();
+__global__ void __launch_bounds__(GA_TPB) k_gather_adj(GatherArgs a) {
+    constexpr int n = N + 1, nn = n * n;
     const DeviceMesh& m = a.m;
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
     const long long KN = m.KN, KS = m.KS;
-    const double mg2 = -0.5 * m.g;
-    for (long long k = (long long)blockIdx.x * GA_WPB + w; k < m.K; k += (long long)gridDim.x * GA_WPB) {
-        const long long base = k * nn, side = k * 4 * n;
-        double bsl[PER];
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            bsl[r] = 0.0;
-            if (node >= nn) continue;
-            const int i = node % n, j = node / n;
-            const long long gid = base + node;
-            double gh = a.Ga[gid], gu = a.Guv[gid], gv = a.Guv[KN + gid], gb = 0.0;
-            auto take = [&](int f, int p) {
-                const long long sl = side + f * n + p;
-                gh += a.Gsl[sl];
-                gu += a.Gsl[KS + sl];
-                gv += a.Gsl[2 * KS + sl];
-                gb += a.Gsl[3 * KS + sl];
-            };
-            if (j == 0) take(0, i);
-            if (i == N) take(1, j);
-            if (j == N) take(2, i);
-            if (i == 0) take(3, j);
-            double ghu = a.Ga[KN + gid], ghv = a.Ga[2 * KN + gid];
-            const double h = a.W[gid];
-            if (h > 0.0) {
-                const double rh = recip_pos(h);
-                gh -= (a.uv[gid] * gu + a.uv[KN + gid] * gv) * rh;
-                ghu = fma(gu, rh, ghu);
-                ghv = fma(gv, rh, ghv);
-            }
-            a.Wbar[gid] += gh;
-            a.Wbar[KN + gid] += ghu;
-            a.Wbar[2 * KN + gid] += ghv;
-            bsl[r] = gb;
-            if (a.bbar && !a.Gsrc) a.bbar[gid] += gb;
-            if (a.bbar && a.Gsrc) {
-                const double cx = mg2 * m.rJ[gid] * a.Gsrc[gid], cy = mg2 * m.rJ[gid] * a.Gsrc[KN + gid];
-                sC[w][0][node] = cx;
-                sC[w][1][node] = cy;
-                sC[w][2][node] = fma(m.axx[gid], cx, m.axy[gid] * cy);
-                sC[w][3][node] = fma(m.aex[gid], cx, m.aey[gid] * cy);
-            }
-        }
-        if (!a.bbar || !a.Gsrc) continue;
-        __syncwarp();
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            if (node >= nn) continue;
-            const int i = node % n, j = node / n;
-            const long long gid = base + node;
-            // (D_xi^T f)(i, j) = sum_q D_qi f(q, j); (D_eta^T f)(i, j) = sum_q D_qj f(i, q)
-            double zx = 0.0, ze = 0.0, tx = 0.0, ty = 0.0, ex = 0.0, ey = 0.0;
-#pragma unroll
-            for (int q = 0; q < n; ++q) {
-                const double di = sD[q * n + i], dj = sD[q * n + j];
-                zx = fma(di, sC[w][2][j * n + q], zx);
-                tx = fma(di, sC[w][0][j * n + q], tx);
-                ty = fma(di, sC[w][1][j * n + q], ty);
-                ze = fma(dj, sC[w][3][q * n + i], ze);
-                ex = fma(dj, sC[w][0][q * n + i], ex);
-                ey = fma(dj, sC[w][1][q * n + i], ey);
-            }
-            const double src = zx + ze + m.axx[gid] * tx + m.axy[gid] * ty + m.aex[gid] * ex + m.aey[gid] * ey;
-            a.bbar[gid] += bsl[r] + src;
-        }
-        __syncwarp();
+    const long long gid = (long long)blockIdx.x * GA_TPB + threadIdx.x;
+    if (gid >= KN) return;
+    const long long k = gid / nn;
+    const int node = (int)(gid - k * nn), i = node % n, j = node / n;
+    const long long side = k * 4 * n;
+    double gh = a.Ga[gid], gu = a.Guv[gid], gv = a.Guv[KN + gid], gb = 0.0;
+    auto take = [&](int f, int p) {
+        const long long sl = side + f * n + p;
+        gh += a.Gsl[sl];
+        gu += a.Gsl[KS + sl];
+        gv += a.Gsl[2 * KS + sl];
+        gb += a.Gsl[3 * KS + sl];
+    };
+    const bool edge = j == 0 || i == N || j == N || i == 0;
+    if (j == 0) take(0, i);
+    if (i == N) take(1, j);
+    if (j == N) take(2, i);
+    if (i == 0) take(3, j);
+    double ghu = a.Ga[KN + gid], ghv = a.Ga[2 * KN + gid];
+    const double h = a.W[gid];
+    if (h > 0.0) {
+        const double rh = recip_pos(h);
+        gh -= (a.uv[gid] * gu + a.uv[KN + gid] * gv) * rh;
+        ghu = fma(gu, rh, ghu);
+        ghv = fma(gv, rh, ghv);
     }
+    a.Wbar[gid] += gh;
+    a.Wbar[KN + gid] += ghu;
+    a.Wbar[2 * KN + gid] += ghv;
+    if (a.bbar && edge) a.bbar[gid] += gb;
 }
 
-// The source part of the gather alone: bbar += (d src / d b)^T Gsrc, for
-// source-coefficient cotangents summed over several stages (the map is
-// linear and depends on the geometry only). One warp per element.
+// ---------------------------------------------------------------------------
+// Source coefficients in reverse: bbar += (d src / d b)^T Gsrc, for one
+// stage's cotangents or their sum over stages (the map is linear and depends
+// on the geometry only). src_c = -(g/2) gamma_c / J (Eq. SourceDisc) with
+//   gamma_x(i,j) = sum_q D_iq (axx_ij + axx_qj) b_qj + sum_q D_jq (aex_ij + aex_iq) b_iq
+// and gamma_y likewise with axy, aey. For i < q on a line the entry
+// D_iq (a_i + a_q) is 4/(w_i w_j) times the volume kernel's pair constant S
+// of the pair, and the reversed entry D_qi (a_q + a_i) is -4/(w_q w_j) S
+// (SBP: w_q D_qi = -w_i D_iq off the diagonal). With c = g fwJ2 Gsrc
+// (= 4/(w_i w_j) times -(g/2) Gsrc / J) at every node, a pair costs four
+// fused multiply-adds,
+//   bbar_q += S_x c_x,i + S_y c_y,i,   bbar_i -= S_x c_x,q + S_y c_y,q,
+// and the diagonal 2 D_ii a_i, nonzero at the two end nodes of a line only
+// (LGL), adds D_ii (w_i w_j / 2) (a_x c_x + a_y c_y) there. One thread per
+// line as in the volume kernels: the xi-line j = l, then the eta-line i = l
+// continuing the node sums in shared memory.
+// ---------------------------------------------------------------------------
 template <int N>
-__global__ void __launch_bounds__(32 * GA_WPB, 5) k_src_adj(DeviceMesh m, const double* __restrict__ Gsrc,
-                                                         double* __restrict__ bbar) {
-    constexpr int n = N + 1, nn = n * n, PER = (nn + 31) / 32;
-    __shared__ double sD[nn];
-    __shared__ double sC[GA_WPB][4][nn];
-    for (int idx = threadIdx.x; idx < nn; idx += blockDim.x) sD[idx] = Dm<N>(idx / n, idx % n);
-    __syncthreads();
-    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+__device__ __forceinline__ void src_pairs_adj(const double* __restrict__ pmk, const double* cxl, const double* cyl,
+                                              double* acc) {
+    constexpr int n = N + 1;
+#pragma unroll
+    for (int i = 0; i < n; ++i)
+#pragma unroll
+        for (int q = i + 1; q < n; ++q) {
+            const double2 c = __ldg(reinterpret_cast<const double2*>(pmk + 2 * pair_index_adj<N>(i, q) * n));
+            acc[q] = fma(c.y, cyl[i], fma(c.x, cxl[i], acc[q]));
+            acc[i] = fma(-c.y, cyl[q], fma(-c.x, cxl[q], acc[i]));
+        }
+}
+
+template <int N>
+__global__ void __launch_bounds__(adj_ne<N>() * (N + 1)) k_src_adj(DeviceMesh m, const double* __restrict__ Gsrc,
+                                                                  double* __restrict__ bbar) {
+    constexpr int n = N + 1, nn = n * n, NE = adj_ne<N>(), NT = NE * n, BLK = NE * nn;
+    constexpr int NP = N * (N + 1) / 2;
+    __shared__ double sc[2][BLK];
+    __shared__ double sacc[BLK];
+    const int t = threadIdx.x;
+    const long long k0 = (long long)blockIdx.x * NE;
     const long long KN = m.KN;
-    const double mg2 = -0.5 * m.g;
-    for (long long k = (long long)blockIdx.x * GA_WPB + w; k < m.K; k += (long long)gridDim.x * GA_WPB) {
-        const long long base = k * nn;
-#pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            if (node >= nn) continue;
-            const long long gid = base + node;
-            const double cx = mg2 * m.rJ[gid] * Gsrc[gid], cy = mg2 * m.rJ[gid] * Gsrc[KN + gid];
-            sC[w][0][node] = cx;
-            sC[w][1][node] = cy;
-            sC[w][2][node] = fma(m.axx[gid], cx, m.axy[gid] * cy);
-            sC[w][3][node] = fma(m.aex[gid], cx, m.aey[gid] * cy);
+    for (int idx = t; idx < BLK; idx += NT) {
+        const int e = idx / nn;
+        const long long k = k0 + e;
+        double cx = 0.0, cy = 0.0;
+        if (k < m.K) {
+            const long long gid = k * nn + (idx - e * nn);
+            const double f = m.g * m.fwJ2[gid];
+            cx = f * Gsrc[gid];
+            cy = f * Gsrc[KN + gid];
         }
-        __syncwarp();
+        sc[0][idx] = cx;
+        sc[1][idx] = cy;
+    }
+    __syncthreads();
+    const int e = t / n, l = t - e * n;
+    const long long k = k0 + e;
+    const bool valid = k < m.K;
+    const double* pmx = m.pm + ((size_t)(valid ? k : 0) * 2 * NP * n + l) * 2;
+    const double* pme = pmx + (size_t)NP * n * 2;
+    const double half_wl = 0.5 * wq<N>(l);
+    const double c0 = Dm<N>(0, 0) * wq<N>(0) * half_wl, cN = Dm<N>(N, N) * wq<N>(N) * half_wl;
+    const int eb = e * nn;
+    double acc[n], cxl[n], cyl[n];
+    // ---- xi-line j = l: nodes (p, l) ----------------------------------------
 #pragma unroll
-        for (int r = 0; r < PER; ++r) {
-            const int node = lane + 32 * r;
-            if (node >= nn) continue;
-            const int i = node % n, j = node / n;
-            const long long gid = base + node;
-            double zx = 0.0, ze = 0.0, tx = 0.0, ty = 0.0, ex = 0.0, ey = 0.0;
+    for (int p = 0; p < n; ++p) {
+        acc[p] = 0.0;
+        cxl[p] = sc[0][eb + l * n + p];
+        cyl[p] = sc[1][eb + l * n + p];
+    }
+    if (valid) {
+        src_pairs_adj<N>(pmx, cxl, cyl, acc);
+        const long long g0 = k * nn + l * n, gN = g0 + N;
+        acc[0] = fma(c0, fma(m.axx[g0], cxl[0], m.axy[g0] * cyl[0]), acc[0]);
+        acc[N] = fma(cN, fma(m.axx[gN], cxl[N], m.axy[gN] * cyl[N]), acc[N]);
+    }
 #pragma unroll
-            for (int q = 0; q < n; ++q) {
-                const double di = sD[q * n + i], dj = sD[q * n + j];
-                zx = fma(di, sC[w][2][j * n + q], zx);
-                tx = fma(di, sC[w][0][j * n + q], tx);
-                ty = fma(di, sC[w][1][j * n + q], ty);
-                ze = fma(dj, sC[w][3][q * n + i], ze);
-                ex = fma(dj, sC[w][0][q * n + i], ex);
-                ey = fma(dj, sC[w][1][q * n + i], ey);
-            }
-            bbar[gid] += zx + ze + m.axx[gid] * tx + m.axy[gid] * ty + m.aex[gid] * ex + m.aey[gid] * ey;
-        }
-        __syncwarp();
+    for (int p = 0; p < n; ++p) sacc[eb + l * n + p] = acc[p];
+    __syncthreads();
+    if (!valid) return;
+    // ---- eta-line i = l: nodes (l, p) ---------------------------------------
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        acc[p] = sacc[eb + p * n + l];
+        cxl[p] = sc[0][eb + p * n + l];
+        cyl[p] = sc[1][eb + p * n + l];
+    }
+    src_pairs_adj<N>(pme, cxl, cyl, acc);
+    {
+        const long long g0 = k * nn + l, gN = g0 + (long long)N * n;
+        acc[0] = fma(c0, fma(m.aex[g0], cxl[0], m.aey[g0] * cyl[0]), acc[0]);
+        acc[N] = fma(cN, fma(m.aex[gN], cxl[N], m.aey[gN] * cyl[N]), acc[N]);
+    }
+#pragma unroll
+    for (int p = 0; p < n; ++p) {
+        const long long gid = k * nn + (long long)p * n + l;
+        bbar[gid] += acc[p];
     }
 }
 
@@ -1110,21 +1120,22 @@ void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* W
                 k_wall_adj<false><<<grid_for(walls, 128), 128, 0, s>>>(m, W, c->w.uv, A.Gfo, A.GUs, av, A.Gsl);
         }
     }
-    GatherArgs ga{m, W, c->w.uv, A.Ga, A.Guv, A.Gsl, defer_src ? nullptr : A.Gsrc, Wbar, bbar};
+    GatherArgs ga{m, W, c->w.uv, A.Ga, A.Guv, A.Gsl, Wbar, bbar};
 #define SWE_GA(NN)                                                                          \
     {                                                                                       \
         Timed tm(c, KC_ADJ, s);                                                             \
-        k_gather_adj<NN><<<grid_for(m.K, GA_WPB), 32 * GA_WPB, 0, s>>>(ga);                 \
+        k_gather_adj<NN><<<grid_for(m.KN, GA_TPB), GA_TPB, 0, s>>>(ga);                     \
     }
     SWE_SWITCH_N_ADJ(m.N, SWE_GA)
 #undef SWE_GA
+    if (bbar && !defer_src) launch_src_adjoint(c, A.Gsrc, bbar, s);
 }
 
 void launch_src_adjoint(swe_ctx* c, const double* Gsrc, double* bbar, cudaStream_t s) {
 #define SWE_SA(NN)                                                                          \
     {                                                                                       \
         Timed tm(c, KC_ADJ, s);                                                             \
-        k_src_adj<NN><<<grid_for(c->m.K, GA_WPB), 32 * GA_WPB, 0, s>>>(c->m, Gsrc, bbar);   \
+        k_src_adj<NN><<<grid_for(c->m.K, adj_ne<NN>()), adj_ne<NN>() * (NN + 1), 0, s>>>(c->m, Gsrc, bbar); \
     }
     SWE_SWITCH_N_ADJ(c->m.N, SWE_SA)
 #undef SWE_SA
