@@ -469,7 +469,7 @@ template <int N, int G, bool VISC>
 __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, bool valid, int sub, double* sc) {
     constexpr int n = N + 1, nn = n * n;
     const DeviceMesh& m = a.m;
-    const double g = m.g;
+    const double g = m.g, g2 = 2.0 * m.g;
     unsigned long long lamb = 0;
     // viscous restriction (VISC, kv > 0): the node's rate gains eps_k kv a^2
     const double ekv = (VISC && valid) ? a.eps[k] * a.kv : 0.0;
@@ -504,19 +504,26 @@ __device__ __forceinline__ void dt_element(const DtArgs& a, long long k, bool va
             const double hm = a.W[own], hp = a.W[nb];
             const double utm = fma(nx, a.uv[own], ny * a.uv[m.KN + own]);
             const double utp = wall ? -utm : fma(nx, a.uv[nb], ny * a.uv[m.KN + nb]);
-            const double ua = 0.5 * (utm + utp);
             const double cm = sc[ownl], cp = wall ? cm : sqrt_pos(g * pos_part(hp));
-            const double ca = 0.5 * (cm + cp);
-            const double ap = fabs(ua + ca), am = fabs(ua - ca);
-            const double A = ap + am, B = ap - am;
-            const double i1 = fma(2.0, ua, A) * rwa;
+            // with s_u = 2 u~_a and s_c = 2 c_a (both sums, no halving):
+            // A = |u~_a + c_a| + |u~_a - c_a| = max(|s_u|, s_c) and
+            // B = |u~_a + c_a| - |u~_a - c_a| = sgn(s_u) min(|s_u|, s_c), the
+            // maximum, minimum and sign taken on the bit patterns
+            const double su = utm + utp, scs = cm + cp;
+            const unsigned long long bau = (unsigned long long)__double_as_longlong(fabs(su)),
+                                     bsc = (unsigned long long)__double_as_longlong(scs);
+            const double A = __longlong_as_double((long long)(bau > bsc ? bau : bsc));
+            const unsigned long long bB =
+                (bau < bsc ? bau : bsc) | ((unsigned long long)__double_as_longlong(su) & 0x8000000000000000ULL);
+            const double B = __longlong_as_double((long long)bB);
+            const double i1 = (su + A) * rwa;
             if ((long long)__double_as_longlong(i1) > 0) invb = max_bits(invb, i1);
             const double jump = utp - utm;
-            // h- > 0 and B [[u~]] < 0 (nonzero factors of opposite signs)
-            const unsigned long long bB = (unsigned long long)__double_as_longlong(B),
-                                     bJ = (unsigned long long)__double_as_longlong(jump);
+            // h- > 0 and B [[u~]] < 0 (nonzero factors of opposite signs);
+            // c_a |B [[u~]]| / (g h-) with c_a = s_c / 2
+            const unsigned long long bJ = (unsigned long long)__double_as_longlong(jump);
             if ((long long)__double_as_longlong(hm) > 0 && ((bB ^ bJ) >> 63) && nonzero(B) && nonzero(jump))
-                invb = max_bits(invb, fabs(ca * B * jump) * rwa * recip_pos(g * hm));
+                invb = max_bits(invb, fabs(scs * B * jump) * rwa * recip_pos(g2 * hm));
         }
         const double inv = seg_max<G>(__longlong_as_double((long long)invb));
         if (valid && sub == 0 && inv > 0.0) atomic_max_pos(&bits[1], inv);
