@@ -967,6 +967,7 @@ extern "C" int swe_entropy(swe_ctx* c, const double* W, double* E, void* stream)
     if (!c || !W || !E) return fail(SWE_ERR_ARG, "swe_entropy: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     double h[4];
+    swe::launch_prim(c, W, s, nullptr);  // the kinetic energy reads the velocities
     swe::launch_reduce(c, W, 1, h, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "swe_entropy");
@@ -991,6 +992,7 @@ extern "C" int swe_integrals(swe_ctx* c, const double* W, double* out4, void* st
     if (!c || !W || !out4) return fail(SWE_ERR_ARG, "swe_integrals: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     double h[4];
+    swe::launch_prim(c, W, s, nullptr);  // the kinetic energy reads the velocities
     swe::launch_reduce(c, W, 2, h, s);
     cudaError_t e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) return cuda_fail(e, "swe_integrals");

@@ -358,6 +358,7 @@ extern "C" int swe_ens_integrals(swe_ens* e, const double* W, double* out, void*
     const int64_t before = sum_launches(e);
     int64_t base = 0;
     for (size_t gi = 0; gi < e->groups.size(); ++gi) {
+        swe::launch_prim(e->groups[gi], W + e->goff[gi], s, nullptr);  // velocities for the kinetic energy
         swe::launch_reduce_inst(e->groups[gi], W + e->goff[gi], e->ebeg[gi], e->integ + 4 * base, s);
         base += e->gcount[gi];
     }

@@ -569,23 +569,36 @@ __global__ void k_copy(long long count, const double* __restrict__ src, double* 
 
 // Device-side rollback of an asynchronous step: where the status word is set,
 // dst gets back src (the state at the start of the failing step).
-__global__ void k_restore(long long count, const double* __restrict__ src, double* __restrict__ dst,
-                          const int* status) {
+// After a failed step (status set): the start state back into W, and the
+// velocities of it (the integrals that follow read them).
+__global__ void k_restore(long long KN, const double* __restrict__ src, double* __restrict__ dst,
+                          double* __restrict__ uv, const int* status) {
     if (*(volatile const int*)status == 0) return;
-    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < count;
-         i += (long long)gridDim.x * blockDim.x)
-        dst[i] = src[i];
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < KN;
+         i += (long long)gridDim.x * blockDim.x) {
+        const double h = src[i], hu = src[KN + i], hv = src[2 * KN + i];
+        dst[i] = h;
+        dst[KN + i] = hu;
+        dst[2 * KN + i] = hv;
+        double u, v;
+        velocities(h, hu, hv, u, v);
+        uv[i] = u;
+        uv[KN + i] = v;
+    }
 }
 
 // ---------------------------------------------------------------------------
 // Diagnostics: sum J w w W (what = 0, three sums), sum J w w e(W) (what = 1,
 // Eq. entropyFunction), or all four (what = 2). Fixed grid, per-block tree
 // sums, then one warp per component adds the partials in a fixed order: the
-// result does not depend on scheduling.
+// result does not depend on scheduling. The kinetic part of e is
+// (hu u + hv v)/2 with the velocities u, v of W (written by the primitives
+// kernel or the stage update that produced W): no reciprocal here, and zero
+// where h <= 0, where u = v = 0.
 // ---------------------------------------------------------------------------
 constexpr int RED_THREADS = 256;
 
-__global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int what,
+__global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, const double* __restrict__ uv, int what,
                               double* __restrict__ part) {
     __shared__ double sh[4][RED_THREADS];
     double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
@@ -599,7 +612,7 @@ __global__ void k_reduce_part(DeviceMesh m, const double* __restrict__ W, int wh
             s2 = fma(wj, hv, s2);
         }
         if (what != 0) {
-            const double kin = kinetic(h, hu, hv);
+            const double kin = 0.5 * fma(hu, uv[id], hv * uv[m.KN + id]);
             const double e = kin + g * h * fma(0.5, h, m.bn[id]);
             s3 = fma(wj, e, s3);
         }
@@ -672,8 +685,8 @@ __global__ void k_reduce_final(const double* __restrict__ part, double* __restri
 // Per-instance integrals of an ensemble group: block i sums the nodes of
 // elements [ebeg[i], ebeg[i+1]) into out[4 i .. 4 i + 3] (mass, momenta,
 // entropy), in a fixed order.
-__global__ void k_reduce_inst(DeviceMesh m, const double* __restrict__ W, const long long* __restrict__ ebeg,
-                              double* __restrict__ out) {
+__global__ void k_reduce_inst(DeviceMesh m, const double* __restrict__ W, const double* __restrict__ uv,
+                              const long long* __restrict__ ebeg, double* __restrict__ out) {
     __shared__ double sh[4][RED_THREADS];
     const long long nn = (long long)m.n * m.n;
     const long long lo = ebeg[blockIdx.x] * nn, hi = ebeg[blockIdx.x + 1] * nn;
@@ -684,7 +697,7 @@ __global__ void k_reduce_inst(DeviceMesh m, const double* __restrict__ W, const 
         s0 = fma(wj, h, s0);
         s1 = fma(wj, hu, s1);
         s2 = fma(wj, hv, s2);
-        const double kin = kinetic(h, hu, hv);
+        const double kin = 0.5 * fma(hu, uv[id], hv * uv[m.KN + id]);
         s3 = fma(wj, kin + g * h * fma(0.5, h, m.bn[id]), s3);
     }
     sh[0][threadIdx.x] = s0;
@@ -803,7 +816,7 @@ void launch_reduce(swe_ctx* c, const double* W, int what, double* host_out, cuda
 void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStream_t s, double* dst) {
     {
         Timed tm(c, KC_REDUCE, s);
-        k_reduce_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->m, W, what, c->w.part);
+        k_reduce_part<<<RED_BLOCKS, RED_THREADS, 0, s>>>(c->m, W, c->w.uv, what, c->w.part);
     }
     Timed tm(c, KC_REDUCE, s);
     double* out = dst ? dst : c->w.part + 4 * RED_BLOCKS;
@@ -814,10 +827,10 @@ void launch_reduce_dev(swe_ctx* c, const double* W, int what, bool pack, cudaStr
 }
 
 void launch_restore(swe_ctx* c, double* W, cudaStream_t s) {
-    const long long count = 3 * c->m.KN;
+    const long long KN = c->m.KN;
     Timed tm(c, KC_UPDATE, s);
-    k_restore<<<grid_for(count, 256) > 4096 ? 4096 : grid_for(count, 256), 256, 0, s>>>(count, c->w.Wn, W,
-                                                                                         c->w.status);
+    k_restore<<<grid_for(KN, 256) > 4096 ? 4096 : grid_for(KN, 256), 256, 0, s>>>(KN, c->w.Wn, W, c->w.uv,
+                                                                                   c->w.status);
 }
 
 void launch_rate(swe_ctx* c, const double* W, const double* R, double* host_out, cudaStream_t s) {
@@ -834,7 +847,7 @@ void launch_rate(swe_ctx* c, const double* W, const double* R, double* host_out,
 
 void launch_reduce_inst(swe_ctx* c, const double* W, const long long* ebeg, double* out, cudaStream_t s) {
     Timed tm(c, KC_REDUCE, s);
-    k_reduce_inst<<<c->m.ninst, RED_THREADS, 0, s>>>(c->m, W, ebeg, out);
+    k_reduce_inst<<<c->m.ninst, RED_THREADS, 0, s>>>(c->m, W, c->w.uv, ebeg, out);
 }
 
 }  // namespace swe

@@ -106,13 +106,6 @@ __device__ __forceinline__ void velocities(double h, double hu, double hv, doubl
     }
 }
 
-// Kinetic energy (hu^2 + hv^2)/(2h) where h > 0, zero where h <= 0.
-__device__ __forceinline__ double kinetic(double h, double hu, double hv) {
-    const double s = 0.5 * fma(hu, hu, hv * hv);
-    if (recip_range(h)) return s * recip_normal(h);
-    return (long long)__double_as_longlong(h) > 0 ? s / h : 0.0;
-}
-
 __device__ __forceinline__ bool stopped(const int* stop) {
     return stop != nullptr && *(volatile const int*)stop != 0;
 }
