@@ -315,9 +315,10 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
                     f_tp.push_back((int32_t)(((long long)kk * 4 + ff) * n + q));
                     f_nx.push_back(nx / js);
                     f_ny.push_back(ny / js);
-                    f_js.push_back(js);
-                    f_sx.push_back(nx);
-                    f_sy.push_back(ny);
+                    // over 8 (exact): the interface flux kernel forms 8 F
+                    f_js.push_back(0.125 * js);
+                    f_sx.push_back(0.125 * nx);
+                    f_sy.push_back(0.125 * ny);
                     f_bm.push_back(bn[own]);
                     f_bp.push_back(bn[nb]);
                 }
@@ -350,7 +351,6 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     m.KS = KS;
     m.g = g;
     m.r2g = 0.5 / g;
-    m.g4 = 0.25 * g;
     cudaError_t e2 = cudaSuccess;
 #define UP(dst, src)                                  \
     dst = dev_upload(c, src, e2);                     \
@@ -359,7 +359,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     UP(m.srcx, srcx) UP(m.srcy, srcy) UP(m.bn, bn) UP(m.nax, cfln) UP(m.rvol, rvol)
     UP(m.fwJ, fwJ) UP(m.fwJ2, fwJ2) UP(m.pm, pm)
     UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
-    UP(m.f_ny, f_ny) UP(m.f_js, f_js) UP(m.f_sx, f_sx) UP(m.f_sy, f_sy) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
+    UP(m.f_ny, f_ny) UP(m.f_js8, f_js) UP(m.f_sx8, f_sx) UP(m.f_sy8, f_sy) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
     UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
     UP(m.w_im, w_im) UP(m.w_tm, w_tm) UP(m.w_nx, w_nx) UP(m.w_ny, w_ny) UP(m.w_js, w_js)
 #undef UP

@@ -321,7 +321,7 @@ __global__ void k_visc_face_adj(DeviceMesh m, const double* __restrict__ Gfvo, d
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long tm = m.f_tm[t], tp = m.f_tp[t];
-        const double nx = 0.5 * m.f_nx[t] * m.f_js[t], ny = 0.5 * m.f_ny[t] * m.f_js[t];
+        const double nx = 4.0 * m.f_nx[t] * m.f_js8[t], ny = 4.0 * m.f_ny[t] * m.f_js8[t];
         const double a2 = Gfvo[tm] - Gfvo[tp], a3 = Gfvo[S + tm] - Gfvo[S + tp];
         const double f2 = nx * a2, g2 = ny * a2, f3 = nx * a3, g3 = ny * a3;
         Gfvtr[tm] = f2;
@@ -549,7 +549,7 @@ __global__ void k_surface_adj(DeviceMesh m, const double* __restrict__ W, const 
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long im = m.f_im[t], ip = m.f_ip[t], tm = m.f_tm[t], tp = m.f_tp[t];
-        const double nx = m.f_nx[t], ny = m.f_ny[t], js = m.f_js[t];
+        const double nx = m.f_nx[t], ny = m.f_ny[t], js = 8.0 * m.f_js8[t];
         const double hm = W[im], hp = W[ip];
         const double um = uv[im], vm = uv[m.KN + im], up = uv[ip], vp = uv[m.KN + ip];
         const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);

@@ -36,54 +36,68 @@ __global__ void k_prim(long long KN, const double* __restrict__ W, double* __res
 // g[[h+b]] - {c}[[u~]]). Writes +F to the owner's side slot and -F to the
 // neighbour's, and the BR1 interface values {u}, {v} to both.
 // ---------------------------------------------------------------------------
-// Flux in the normal frame from the rotated traces (u~, v~) of both sides;
-// g4 = g/4 and r2g = 1/(2g) are the context's constants. With
-// c_a = {c} = c4m + c4p, c4 = sqrt(g4 max(h, 0)) = c/2, the half-weighted
-// projections of the dissipation are
-//   s1 = |{u~} + {c}| (({c}/(2g)) [[u~]] + [[h+b]]/2),
-//   s3 = |{u~} - {c}| (-({c}/(2g)) [[u~]] + [[h+b]]/2),
-// and the EC flux's pressure term g {h^2}/2 = g4 (h-^2 + h+^2).
+// Eight times the flux in the normal frame, from sums and differences of the
+// two sides: H = h- + h+, U = u~- + u~+, V = v~- + v~+ (twice the averages),
+// du = [[u~]], dv = [[v~]], C = c- + c+ with c = sqrt(g max(h, 0)) (twice
+// {c}) and f = H U (four times the EC mass flux {h}{u~}). With the
+// dissipation's projections scaled by four,
+//   S1 = |U + C| (C/(2g) du + [[h+b]]),   S3 = |U - C| (-C/(2g) du + [[h+b]]),
+// D = S1 + S3 and r2g = 1/(2g), g2 = 2g:
+//   8 F1 = 2f - D,
+//   8 F2 = f U + g2 (h-^2 + h+^2) - (U D + C (S1 - S3))/2,
+//   8 F3 = f V - V D/2 - |f| dv,
+// the EC flux of Eq. surfaceFluxes minus 1/2 R~|Lambda~|R~^T [[q~]] with the
+// averages written as half sums; the factor 8 is in the rotation back
+// (the face planes hold the normals and surface Jacobians divided by 8, an
+// exact scaling).
 template <bool ES>
-__device__ __forceinline__ void normal_flux(double g4, double r2g, double hm, double hp, double utm, double utp,
-                                            double vtm, double vtp, double bm, double bp, double& F1, double& F2,
-                                            double& F3) {
-    const double ha = 0.5 * (hm + hp), ua = 0.5 * (utm + utp), va = 0.5 * (vtm + vtp);
-    const double F1ec = ha * ua;
-    F1 = F1ec;
-    F2 = fma(F1ec, ua, g4 * fma(hm, hm, hp * hp));
-    F3 = F1ec * va;
+__device__ __forceinline__ void normal_flux8(double g, double g2, double r2g, double hm, double hp, double U,
+                                             double V, double du, double dv, double bm, double bp, double& F1,
+                                             double& F2, double& F3) {
+    const double f = (hm + hp) * U;
+    F2 = fma(f, U, g2 * fma(hm, hm, hp * hp));
+    F3 = f * V;
     if (ES) {
-        const double ca = sqrt_pos(g4 * pos_part(hm)) + sqrt_pos(g4 * pos_part(hp));
-        const double jH = 0.5 * ((hp + bp) - (hm + bm));
-        const double cr = ca * r2g;
-        const double dut = utp - utm, dvt = vtp - vtm;
-        const double s1 = fabs(ua + ca) * fma(cr, dut, jH);
-        const double s3 = fabs(ua - ca) * fma(-cr, dut, jH);
-        const double d1 = s1 + s3;
-        F1 = fma(-0.5, d1, F1);
-        F2 = fma(-0.5, fma(ua, d1, ca * (s1 - s3)), F2);
-        F3 = fma(-0.5, fma(va, d1, fabs(F1ec) * dvt), F3);
+        const double C = sqrt_pos(g * pos_part(hm)) + sqrt_pos(g * pos_part(hp));
+        const double jH = (hp + bp) - (hm + bm);
+        const double Cr = C * r2g;
+        const double S1 = fabs(U + C) * fma(Cr, du, jH);
+        const double S3 = fabs(U - C) * fma(-Cr, du, jH);
+        const double D = S1 + S3;
+        F1 = fma(2.0, f, -D);
+        F2 = fma(-0.5, fma(U, D, C * (S1 - S3)), F2);
+        F3 = fma(-fabs(f), dv, fma(-0.5 * V, D, F3));
+    } else {
+        F1 = 2.0 * f;
     }
 }
 
+// Interface flux through the owner's outward normal at every unique face
+// node (Eq. NumericalSurfaceFlux evaluated in the normal frame, App. B):
+// the velocity sums and jumps rotated into the frame (Eq.
+// rotatingVelocities), the flux of normal_flux8, rotated back (Eq.
+// surfaceFlux2DRotated) with the unscaled normal over 8, whose length is the
+// surface Jacobian over 8. Writes +F to the owner's side slot and -F to the
+// neighbour's, and the BR1 interface values {u}, {v} to both.
 template <bool ES>
 __global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const double* __restrict__ uv,
                           double* __restrict__ Fout, double* __restrict__ Ustar, const int* stop) {
     if (stopped(stop)) return;
     const long long total = (long long)m.nfaces * m.n;
+    const double g = m.g, g2 = 2.0 * m.g;
     for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
          t += (long long)gridDim.x * blockDim.x) {
         const long long im = m.f_im[t], ip = m.f_ip[t], tm = m.f_tm[t], tp = m.f_tp[t];
         const double nx = m.f_nx[t], ny = m.f_ny[t];
         const double hm = W[im], hp = W[ip];
         const double um = uv[im], vm = uv[m.KN + im], up = uv[ip], vp = uv[m.KN + ip];
-        const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
-        const double utp = fma(nx, up, ny * vp), vtp = fma(nx, vp, -ny * up);
+        const double su = um + up, sv = vm + vp, ju = up - um, jv = vp - vm;
+        const double U = fma(nx, su, ny * sv), V = fma(nx, sv, -ny * su);
+        const double du = fma(nx, ju, ny * jv), dv = fma(nx, jv, -ny * ju);
         double F1, F2, F3;
-        normal_flux<ES>(m.g4, m.r2g, hm, hp, utm, utp, vtm, vtp, m.f_bm[t], m.f_bp[t], F1, F2, F3);
-        // rotate back with the unscaled normal (the surface Jacobian included)
-        const double sx = m.f_sx[t], sy = m.f_sy[t];
-        const double G1 = m.f_js[t] * F1;
+        normal_flux8<ES>(g, g2, m.r2g, hm, hp, U, V, du, dv, m.f_bm[t], m.f_bp[t], F1, F2, F3);
+        const double sx = m.f_sx8[t], sy = m.f_sy8[t];
+        const double G1 = m.f_js8[t] * F1;
         const double G2 = fma(sx, F2, -sy * F3);
         const double G3 = fma(sy, F2, sx * F3);
         Fout[tm] = G1;
@@ -92,7 +106,7 @@ __global__ void k_surface(DeviceMesh m, const double* __restrict__ W, const doub
         Fout[tp] = negated(G1);
         Fout[m.KS + tp] = negated(G2);
         Fout[2 * m.KS + tp] = negated(G3);
-        const double us = 0.5 * (um + up), vs = 0.5 * (vm + vp);
+        const double us = 0.5 * su, vs = 0.5 * sv;
         Ustar[tm] = us;
         Ustar[m.KS + tm] = vs;
         Ustar[tp] = us;
@@ -115,11 +129,13 @@ __global__ void k_wall(DeviceMesh m, const double* __restrict__ W, const double*
         const double nx = m.w_nx[t], ny = m.w_ny[t], js = m.w_js[t];
         const double hm = W[im], um = uv[im], vm = uv[m.KN + im], bm = m.bn[im];
         const double utm = fma(nx, um, ny * vm), vtm = fma(nx, vm, -ny * um);
+        // mirror state: U = 0, V = 2 v~, du = -2 u~, dv = 0
         double F1, F2, F3;
-        normal_flux<ES>(m.g4, m.r2g, hm, hm, utm, -utm, vtm, vtm, bm, bm, F1, F2, F3);
-        Fout[tm] = js * F1;
-        Fout[m.KS + tm] = js * fma(nx, F2, -ny * F3);
-        Fout[2 * m.KS + tm] = js * fma(ny, F2, nx * F3);
+        normal_flux8<ES>(m.g, 2.0 * m.g, m.r2g, hm, hm, 0.0, 2.0 * vtm, -2.0 * utm, 0.0, bm, bm, F1, F2, F3);
+        const double js8 = 0.125 * js;
+        Fout[tm] = js8 * F1;
+        Fout[m.KS + tm] = js8 * fma(nx, F2, -ny * F3);
+        Fout[2 * m.KS + tm] = js8 * fma(ny, F2, nx * F3);
         Ustar[tm] = um;
         Ustar[m.KS + tm] = vm;
     }
@@ -186,9 +202,10 @@ __global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, const
             const double F3 = (vm ? Fvtr[S + tm] : 0.0) + (vp ? Fvtr[S + tp] : 0.0);
             const double G2 = (vm ? Fvtr[2 * S + tm] : 0.0) + (vp ? Fvtr[2 * S + tp] : 0.0);
             const double G3 = (vm ? Fvtr[3 * S + tm] : 0.0) + (vp ? Fvtr[3 * S + tp] : 0.0);
-            const double nx = m.f_sx[t], ny = m.f_sy[t];
-            a2 = 0.5 * fma(nx, F2, ny * G2);
-            a3 = 0.5 * fma(nx, F3, ny * G3);
+            // (the unscaled normal over 8: 4 times it is half the normal, exactly)
+            const double nx = m.f_sx8[t], ny = m.f_sy8[t];
+            a2 = 4.0 * fma(nx, F2, ny * G2);
+            a3 = 4.0 * fma(nx, F3, ny * G3);
         }
         Fvout[tm] = a2;
         Fvout[S + tm] = a3;

@@ -76,7 +76,6 @@ struct DeviceMesh {
     long long KS;       // K*4*n
     double g;
     double r2g;         // 0.5 / g (the interface dissipation's eigenvalue scale)
-    double g4;          // g / 4
     // per node
     const double* axx;  // contravariant xi vector (y_eta, -x_eta)
     const double* axy;
@@ -103,9 +102,9 @@ struct DeviceMesh {
     const int32_t* f_tp;   // neighbour side slot
     const double* f_nx;    // owner outward unit normal
     const double* f_ny;
-    const double* f_js;    // surface Jacobian |outward unscaled normal|
-    const double* f_sx;    // owner outward unscaled normal (unit normal times f_js)
-    const double* f_sy;
+    const double* f_js8;   // surface Jacobian |outward unscaled normal| / 8
+    const double* f_sx8;   // owner outward unscaled normal / 8 (unit normal times f_js8)
+    const double* f_sy8;
     const double* f_bm;    // bathymetry on both sides
     const double* f_bp;
     // per element side node
