@@ -255,7 +255,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         }
 
     // ---- unique faces and element sides ----
-    std::vector<int32_t> f_im, f_ip, f_tm, f_tp, s_nb(KS), w_im, w_tm;
+    std::vector<int32_t> f_im, f_ip, f_tm, f_tp, s_nb(KS), s_face(KS, -1), w_im, w_tm;
     std::vector<double> f_nx, f_ny, f_js, f_sx, f_sy, f_bm, f_bp, s_nx(KS), s_ny(KS), s_rwa(KS), w_nx, w_ny, w_js;
     const double w0 = w[0];
     auto outward = [&](int k, int f, int i, int j, double& nx, double& ny) {
@@ -309,6 +309,8 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
                 s_ny[slot] = ny / js;
                 s_rwa[slot] = js / (w0 * Jv[own]);
                 if (kk > k || (kk == k && ff > f)) {
+                    s_face[slot] = (int32_t)f_im.size();
+                    s_face[((long long)kk * 4 + ff) * n + q] = (int32_t)f_im.size();
                     f_im.push_back((int32_t)own);
                     f_ip.push_back((int32_t)nb);
                     f_tm.push_back((int32_t)slot);
@@ -360,7 +362,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     UP(m.fwJ, fwJ) UP(m.fwJ2, fwJ2) UP(m.pm, pm)
     UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
     UP(m.f_ny, f_ny) UP(m.f_js8, f_js) UP(m.f_sx8, f_sx) UP(m.f_sy8, f_sy) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
-    UP(m.s_nb, s_nb) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
+    UP(m.s_nb, s_nb) UP(m.s_face, s_face) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)
     UP(m.w_im, w_im) UP(m.w_tm, w_tm) UP(m.w_nx, w_nx) UP(m.w_ny, w_ny) UP(m.w_js, w_js)
 #undef UP
     m.nae = nullptr;
@@ -399,11 +401,11 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     }
     if (p->av) {
         void* q = nullptr;
-        e2 = cudaMalloc(&q, (size_t)K + 16);
+        e2 = cudaMalloc(&q, sizeof(uint32_t) * ((size_t)K + 4));
         if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }
         c->allocations.push_back(q);
-        W.touch = static_cast<uint8_t*>(q);
-        cudaMemset(W.touch, 0, (size_t)K);
+        W.touch = static_cast<uint32_t*>(q);
+        cudaMemset(W.touch, 0, sizeof(uint32_t) * (size_t)K);
         q = nullptr;
         e2 = cudaMalloc(&q, sizeof(int) * ((size_t)K + 4));
         if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: allocation"); }

@@ -167,46 +167,54 @@ __global__ void k_ustar(DeviceMesh m, const double* __restrict__ uv, double* __r
 // BR1 viscous interface flux {F^v . n} (Thm. 1) with the owner's unscaled
 // outward normal; +avg to the owner's slot, -avg to the neighbour's. Only
 // viscous elements (eps_k > 0) carry side-node viscous fluxes: the other
-// side's traces count as zero and are not read, and a face between two
-// inviscid elements gets zero without reading any.
+// side's traces count as zero and are not read.
 // ---------------------------------------------------------------------------
 //
-// The same launch marks the elements a viscous flux reaches (touch[k] = 1
-// where k or a face neighbour is viscous, else 0), so that the volume kernel
-// skips the viscous lifts of all other elements with one byte per element
-// (the neighbour of face f: the element of the node meeting the face's first
-// node; s_nb < 0 is a wall, which carries no viscous flux).
+// Only the faces of the viscous elements are visited (the list of the AV
+// indicator kernel, one thread per side slot): every other face carries no
+// viscous flux, and its slots (which may hold the values of an earlier
+// state) are not read (below). A face between two viscous elements is
+// evaluated by its owner's visit only.
+//
+// The same launch writes the side masks of the volume kernel, one pass over
+// the elements: bit f of touch[k] is set where a viscous flux crosses side f
+// of element k (k viscous, walls included, or its face-f neighbour viscous);
+// the volume kernel reads the viscous interface flux of exactly those sides.
 __global__ void k_visc_face(DeviceMesh m, const double* __restrict__ Fvtr, const double* __restrict__ eps,
-                            double* __restrict__ Fvout, uint8_t* __restrict__ touch, const int* stop) {
+                            const int* __restrict__ vlist, const int* __restrict__ vcount,
+                            double* __restrict__ Fvout, uint32_t* __restrict__ touch, const int* stop) {
     if (stopped(stop)) return;
-    const long long total = (long long)m.nfaces * m.n;
     const long long S = m.KS, sps = 4LL * m.n;  // side slots per element
     const long long nn = (long long)m.n * m.n;
     for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < m.K;
          k += (long long)gridDim.x * blockDim.x) {
-        bool t = nonzero(eps[k]);
+        const bool vk = nonzero(eps[k]);
+        unsigned mask = 0u;
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
             const long long nb = m.s_nb[k * sps + f * m.n];
-            t |= nb >= 0 && nonzero(eps[nb / nn]);
+            if (vk || (nb >= 0 && nonzero(eps[nb / nn]))) mask |= 1u << f;
         }
-        touch[k] = t ? 1 : 0;
+        touch[k] = mask;
     }
-    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < total;
-         t += (long long)gridDim.x * blockDim.x) {
+    const long long work = (long long)*vcount * sps;
+    for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < work;
+         w += (long long)gridDim.x * blockDim.x) {
+        const long long k = vlist[w / sps];
+        const long long sl = k * sps + w % sps;
+        const int t = m.s_face[sl];
+        if (t < 0) continue;  // solid wall: no viscous flux, the slot stays zero
         const long long tm = m.f_tm[t], tp = m.f_tp[t];
         const bool vm = nonzero(eps[tm / sps]), vp = nonzero(eps[tp / sps]);
-        double a2 = 0.0, a3 = 0.0;
-        if (vm || vp) {
-            const double F2 = (vm ? Fvtr[tm] : 0.0) + (vp ? Fvtr[tp] : 0.0);
-            const double F3 = (vm ? Fvtr[S + tm] : 0.0) + (vp ? Fvtr[S + tp] : 0.0);
-            const double G2 = (vm ? Fvtr[2 * S + tm] : 0.0) + (vp ? Fvtr[2 * S + tp] : 0.0);
-            const double G3 = (vm ? Fvtr[3 * S + tm] : 0.0) + (vp ? Fvtr[3 * S + tp] : 0.0);
-            // (the unscaled normal over 8: 4 times it is half the normal, exactly)
-            const double nx = m.f_sx8[t], ny = m.f_sy8[t];
-            a2 = 4.0 * fma(nx, F2, ny * G2);
-            a3 = 4.0 * fma(nx, F3, ny * G3);
-        }
+        if (sl == tp && vm) continue;  // the owner, viscous too, evaluates the face
+        const double F2 = (vm ? Fvtr[tm] : 0.0) + (vp ? Fvtr[tp] : 0.0);
+        const double F3 = (vm ? Fvtr[S + tm] : 0.0) + (vp ? Fvtr[S + tp] : 0.0);
+        const double G2 = (vm ? Fvtr[2 * S + tm] : 0.0) + (vp ? Fvtr[2 * S + tp] : 0.0);
+        const double G3 = (vm ? Fvtr[3 * S + tm] : 0.0) + (vp ? Fvtr[3 * S + tp] : 0.0);
+        // (the unscaled normal over 8: 4 times it is half the normal, exactly)
+        const double nx = m.f_sx8[t], ny = m.f_sy8[t];
+        const double a2 = 4.0 * fma(nx, F2, ny * G2);
+        const double a3 = 4.0 * fma(nx, F3, ny * G3);
         Fvout[tm] = a2;
         Fvout[S + tm] = a3;
         Fvout[tp] = negated(a2);
@@ -793,10 +801,14 @@ void launch_ustar(swe_ctx* c, cudaStream_t s) {
 }
 
 void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop) {
-    const long long total = (long long)c->m.nfaces * c->m.n;
-    const long long work = total > c->m.K ? total : c->m.K;
+    // a fixed grid striding over the elements and over the viscous elements'
+    // side slots (their number is known on the device only): sixteen blocks
+    // per SM at most
+    const long long most = (long long)c->m.K * 4 * c->m.n;
+    const int blocks = grid_for(most, 128) < 16 * c->sms ? grid_for(most, 128) : 16 * c->sms;
     Timed tm(c, KC_VFACE, s);
-    k_visc_face<<<grid_for(work, 128), 128, 0, s>>>(c->m, c->w.Fvtr, c->w.eps, c->w.Fvout, c->w.touch, stop);
+    k_visc_face<<<blocks, 128, 0, s>>>(c->m, c->w.Fvtr, c->w.eps, c->w.vlist, c->w.vcount, c->w.Fvout, c->w.touch,
+                                       stop);
 }
 
 void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,

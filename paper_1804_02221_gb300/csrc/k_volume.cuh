@@ -60,7 +60,7 @@ struct VolArgs {
     const double* Fvout;
     const double* Lv;
     const double* eps;
-    const uint8_t* touch;  // 1 where a viscous flux reaches the element (viscous face kernel)
+    const uint32_t* touch;  // bit f: a viscous flux crosses side f (viscous face kernel)
     double* R;
     const int* stop;
 };
@@ -204,10 +204,11 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     const long long side = (valid ? k : 0) * 4 * n;
     const double ek = (AV && valid) ? a.eps[k] : 0.0;
     const bool visc = ek > 0.0;
-    // a viscous interface flux reaches the element only where it or a face
-    // neighbour is viscous; elsewhere the viscous lifts are exactly zero and
-    // are skipped without reading them
-    const bool touch = AV && valid && a.touch[k] != 0;
+    // a viscous interface flux crosses side f only where the element or its
+    // face-f neighbour is viscous (bit f of the mask); elsewhere the viscous
+    // lift is exactly zero and is skipped without reading the slot
+    const unsigned tmask = (AV && valid) ? a.touch[k] : 0u;
+    const bool touch = tmask != 0u;
     double A1[n], A2[n], A3[n], B2[n], B3[n];
 
     // ---- xi-line j = l ----------------------------------------------------
@@ -242,17 +243,15 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             A1[p] += t1;
             A2[p] = fma(-S(F_U)[nd], t1, fma(wl, a.Fout[KS + sl], A2[p]));
             A3[p] = fma(-S(F_V)[nd], t1, fma(wl, a.Fout[2 * KS + sl], A3[p]));
-            if (AV && touch) {
-                // viscous lift -w_l (F^v*_out - own outward flux); skipped
-                // where no viscous flux reaches the face (both sides inviscid)
+            if (AV && ((tmask >> f) & 1u)) {
+                // viscous lift -w_l (F^v*_out - own outward flux) where a
+                // viscous flux crosses the side
                 const double fv2 = a.Fvout[sl], fv3 = a.Fvout[KS + sl];
-                if (visc || nonzero(fv2) || nonzero(fv3)) {
-                    const double sg = end == 0 ? 1.0 : -1.0;
-                    const double own2 = visc ? sg * a.Fvt[gid0 + p] : 0.0;
-                    const double own3 = visc ? sg * a.Fvt[m.KN + gid0 + p] : 0.0;
-                    A2[p] = fma(-wl, fv2 - own2, A2[p]);
-                    A3[p] = fma(-wl, fv3 - own3, A3[p]);
-                }
+                const double sg = end == 0 ? 1.0 : -1.0;
+                const double own2 = visc ? sg * a.Fvt[gid0 + p] : 0.0;
+                const double own3 = visc ? sg * a.Fvt[m.KN + gid0 + p] : 0.0;
+                A2[p] = fma(-wl, fv2 - own2, A2[p]);
+                A3[p] = fma(-wl, fv3 - own3, A3[p]);
             }
         }
     }
@@ -322,11 +321,11 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
                 a3 = fma(-wij, a.Lv[m.KN + gid], a3);
             }
             // viscous lift at sides 0 and 2: -(tangential weight) (F^v*_out -
-            // own outward flux), skipped where no viscous flux reaches the face
+            // own outward flux), where a viscous flux crosses the side
             auto vlift = [&](int f, double sg) {
                 const long long sl = side + f * n + i;
-                const double fv2 = a.Fvout[sl], fv3 = a.Fvout[KS + sl];
-                if (visc || nonzero(fv2) || nonzero(fv3)) {
+                if ((tmask >> f) & 1u) {
+                    const double fv2 = a.Fvout[sl], fv3 = a.Fvout[KS + sl];
                     const double own2 = visc ? sg * a.Fvt[2 * m.KN + gid] : 0.0;
                     const double own3 = visc ? sg * a.Fvt[3 * m.KN + gid] : 0.0;
                     a2 = fma(-wi, fv2 - own2, a2);
@@ -435,7 +434,8 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
         }
     }
     const bool visc = AV && a.eps[k] > 0.0;
-    if (AV && a.touch[k] != 0) {
+    const unsigned tmask = AV ? a.touch[k] : 0u;
+    if (AV && tmask != 0u) {
         if (visc) {
             // the volume part of the viscous divergence (AV kernel)
 #pragma unroll
@@ -448,16 +448,16 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
                 }
             }
         }
-        // viscous lifts -(tangential weight) (F^v*_out - own outward flux),
-        // skipped where no viscous flux reaches the face (both sides inviscid)
+        // viscous lifts -(tangential weight) (F^v*_out - own outward flux)
+        // where a viscous flux crosses the side
 #pragma unroll
         for (int f = 0; f < 4; ++f) {
 #pragma unroll
             for (int p = 0; p < n; ++p) {
                 const int d = side_node<N>(f, p);
                 const long long sl = side + f * n + p;
-                const double fv2 = a.Fvout[sl], fv3 = a.Fvout[m.KS + sl];
-                if (visc || nonzero(fv2) || nonzero(fv3)) {
+                if ((tmask >> f) & 1u) {
+                    const double fv2 = a.Fvout[sl], fv3 = a.Fvout[m.KS + sl];
                     const double sg = (f == 1 || f == 2) ? 1.0 : -1.0;
                     const long long pl = (f == 1 || f == 3) ? 0 : 2 * m.KN;  // F~v on xi sides, G~v on eta sides
                     const double own2 = visc ? sg * a.Fvt[pl + g0 + d] : 0.0;

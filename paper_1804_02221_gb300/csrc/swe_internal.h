@@ -109,6 +109,7 @@ struct DeviceMesh {
     const double* f_bp;
     // per element side node
     const int32_t* s_nb;   // node id of the neighbour's matching node (-1: solid wall)
+    const int32_t* s_face; // unique face node (index into the f_* arrays) of the slot (-1: solid wall)
     const double* s_nx;    // own outward unit normal
     const double* s_ny;
     const double* s_rwa;   // 1/(omega_0 a), a = J/Jsurf (Lemma PosPres)
@@ -135,7 +136,7 @@ struct Work {
     double* Fvout;  // [2][KS] outward viscous interface flux
     double* Lv;     // [2][KN] volume part of the viscous divergence, sum_q D_iq F~v + D_jq G~v
                     // (components 2, 3; written and read for viscous elements only)
-    uint8_t* touch; // [K] 1 where the element or a face neighbour is viscous (viscous face kernel)
+    uint32_t* touch; // [K] bit f: a viscous flux crosses side f (the element or its face-f neighbour is viscous)
     int* vlist;     // [K] viscous elements (AV indicator), vcount of them
     int* vcount;
     double* eps;    // [K]

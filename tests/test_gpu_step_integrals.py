@@ -67,6 +67,23 @@ def test_failed_step_restores_state_and_bad_arguments():
     assert np.array_equal(got, c.integrals(W))
 
 
+def test_failed_async_step_restores_state_and_its_integrals():
+    """swe_step_async that fails restores W on the device; the integrals it
+    leaves in out (read from the velocities, which the restore rewrites) are
+    bitwise those of the restored state, and the status bits are set."""
+    swedg = swe_mod()
+    p = I.random_rough(N=3, K1=4, seed=9, dry_fraction=0.5)
+    kw = dict(flux=1, limiter=True, rk=1)
+    c = swedg.SweContext.from_problem(p, **kw)
+    W0, _ = O.Oracle(p, **kw).limit(p.W)
+    W = dev(W0)
+    out = c.step_async(W, 5.0, 1)   # far above the admissible step size
+    got = out.cpu().numpy()
+    assert int(got[5]) != 0
+    assert np.array_equal(W.cpu().numpy(), W0)
+    assert np.array_equal(got[:4], c.integrals(W))
+
+
 def test_integrals_against_oracle_after_steps():
     """Mass conservation and the oracle's integrals of the GPU state."""
     swedg = swe_mod()
