@@ -151,6 +151,10 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     // ---- host geometry (Sec. 2.1) ----
     std::vector<double> axx(KN), axy(KN), aex(KN), aey(KN), rJ(KN), wJ(KN), srcx(KN), srcy(KN), bn(KN),
         cfln(KN), rvol(K), Jv(KN);
+    // the source as the start of the split volume kernel's pressure sums
+    // (degrees with pressure sums only; empty otherwise)
+    const bool psums = p->volume == 0 && N >= 5;
+    std::vector<double> ssx(psums ? KN : 0), ssy(psums ? KN : 0);
     std::vector<double> tmp(4 * nn);
     for (int k = 0; k < K; ++k) {
         const double* X = x + (size_t)k * nn;
@@ -219,6 +223,14 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
                 const double gy = axy[id] * bx + d2 + aey[id] * be + d3;
                 srcx[id] = -0.5 * g * gx * rJ[id];
                 srcy[id] = -0.5 * g * gy * rJ[id];
+                // h srcx = f (2g h) ssx with f = -1/(w_i w_j J): the source
+                // joins the node's pressure sums sum_q h_q Sx before they
+                // are scaled by 2g h (w_i w_j gamma / 4 = sum_q b_q Sx over
+                // both lines of the node, with the pair constants' Sx)
+                if (psums) {
+                    ssx[id] = 0.25 * w[i] * w[j] * gx;
+                    ssy[id] = 0.25 * w[i] * w[j] * gy;
+                }
             }
     }
 
@@ -359,7 +371,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: upload"); }
     UP(m.axx, axx) UP(m.axy, axy) UP(m.aex, aex) UP(m.aey, aey) UP(m.rJ, rJ) UP(m.wJ, wJ)
     UP(m.srcx, srcx) UP(m.srcy, srcy) UP(m.bn, bn) UP(m.nax, cfln) UP(m.rvol, rvol)
-    UP(m.fwJ, fwJ) UP(m.fwJ2, fwJ2) UP(m.pm, pm)
+    UP(m.fwJ, fwJ) UP(m.fwJ2, fwJ2) UP(m.pm, pm) UP(m.ssx, ssx) UP(m.ssy, ssy)
     UP(m.f_im, f_im) UP(m.f_ip, f_ip) UP(m.f_tm, f_tm) UP(m.f_tp, f_tp) UP(m.f_nx, f_nx)
     UP(m.f_ny, f_ny) UP(m.f_js8, f_js) UP(m.f_sx8, f_sx) UP(m.f_sy8, f_sy) UP(m.f_bm, f_bm) UP(m.f_bp, f_bp)
     UP(m.s_nb, s_nb) UP(m.s_face, s_face) UP(m.s_nx, s_nx) UP(m.s_ny, s_ny) UP(m.s_rwa, s_rwa)

@@ -27,11 +27,16 @@
 //    1 for P, 2 for the mass sums, 8 fused multiply-adds for the momenta).
 //    From N = 5 up the pressure parts P Sx = p_i (h_q Sx) are summed per
 //    node as h_q Sx (B2, B3) and scaled by the node's p = 2g h once per line:
-//    14 per pair.
+//    14 per pair. The eta-line sums start from w_i w_j gamma / 4 (the split
+//    bathymetry source, sum_q b_q Sx over both lines), so the scaling also
+//    forms the source term h srcx and the end takes one product less per
+//    momentum component.
 //  * One thread per element line: it runs its xi-line, hands the results
-//    through shared memory, then runs the eta-line with the same index
-//    starting from them, and finishes the nodes of that column (interface
-//    lifts, viscous terms, source, scaling by -1/(w_i w_j J)) in registers.
+//    over (through shared memory, or at N = 7 by a transpose across the
+//    element's eight lanes with warp shuffles, pressure sums included), then
+//    runs the eta-line with the same index starting from them, and finishes
+//    the nodes of that column (interface lifts, viscous terms, source,
+//    scaling by -1/(w_i w_j J)) in registers.
 //  * The volume part of the viscous divergence (sum_q D_iq F~v + D_jq G~v)
 //    of the few viscous elements comes from the AV kernel (Lv); here it is
 //    weighted by -w_i w_j and added, with the viscous interface lifts. A
@@ -71,9 +76,36 @@ constexpr int vol_ne() {
     return (TPB / (N + 1)) > 0 ? TPB / (N + 1) : 1;
 }
 
+// Pressure parts of the pair fluxes summed per node (14 FP64 instructions
+// per pair and 4 per node instead of 15 per pair): a gain from N = 5 up
+// (measured; at N = 3 the per-node products cost more than the pairs save).
+template <int N>
+constexpr bool vol_pressure_sums() {
+    return N >= 5;
+}
+
+// The xi -> eta hand-over through warp shuffles. Where n = N + 1 is a power
+// of two (N = 7 of the built degrees), every element's n lines are n
+// consecutive lanes of one warp, and the hand-over is an n x n transpose of
+// each accumulator across those lanes. The pressure sums then travel with
+// the other accumulators unscaled and are scaled by 2g h once per node, after
+// the eta-line (2 FP64 instructions per node fewer); the block stages only
+// the five state planes and needs no second barrier.
+template <int N>
+constexpr bool vol_shfl() {
+    return vol_pressure_sums<N>() && ((N + 1) & N) == 0 && N + 1 <= 32;
+}
+
+// Shared-memory planes: the staged state (and 2g h, and the hand-over
+// planes, where the hand-over goes through shared memory).
+template <int N>
+constexpr int vol_planes() {
+    return vol_shfl<N>() ? (int)F_P : (int)F_COUNT;
+}
+
 template <int N, bool AV, int TPB>
 constexpr size_t vol_smem() {
-    return sizeof(double) * ((size_t)F_COUNT * vol_ne<N, TPB>() * (N + 1) * (N + 1));
+    return sizeof(double) * ((size_t)vol_planes<N>() * vol_ne<N, TPB>() * (N + 1) * (N + 1));
 }
 
 // Shapes whose staging exceeds the 227 KB of shared memory a block may use
@@ -86,21 +118,41 @@ constexpr bool vol_fits() {
 // Blocks per SM that the shared memory admits (228 KB per SM, 1 KB reserved
 // per block), passed to __launch_bounds__ so that the register allocation
 // does not lower the occupancy below what the staging allows.
+// With the shuffle hand-over the staging admits more blocks than the
+// registers of the pair loops allow; there the bound keeps 168 registers a
+// thread (the budget of the shared-memory hand-over at N = 7).
 template <int N, bool AV, int TPB>
 constexpr int vol_min_blocks() {
-    constexpr int warps = (vol_ne<N, TPB>() * (N + 1) + 31) / 32;
+    constexpr int threads = vol_ne<N, TPB>() * (N + 1);
+    constexpr int warps = (threads + 31) / 32;
     constexpr int by_smem = (int)((228 * 1024) / (vol_smem<N, AV, TPB>() + 1024));
     constexpr int by_warps = 64 / warps;
-    constexpr int b = by_smem < by_warps ? by_smem : by_warps;
+    constexpr int by_regs = vol_shfl<N>() ? 65536 / (threads * 168) : 64;
+    constexpr int b0 = by_smem < by_warps ? by_smem : by_warps;
+    constexpr int b = b0 < by_regs ? b0 : by_regs;
     return b > 0 ? b : 1;
 }
 
-// Pressure parts of the pair fluxes summed per node (14 FP64 instructions
-// per pair and 4 per node instead of 15 per pair): a gain from N = 5 up
-// (measured; at N = 3 the per-node products cost more than the pairs save).
-template <int N>
-constexpr bool vol_pressure_sums() {
-    return N >= 5;
+// In-place transpose across the n lanes l = 0..n-1 of an element (n a power
+// of two, the lanes consecutive and aligned within the warp): lane l holds
+// row l of an n x n array on entry and column l on return. For each bit M of
+// the lane index, lanes l and l^M exchange the entries whose index differs
+// from the lane's in bit M; after all bits, entry p of lane l came from
+// entry l of lane p. Every lane of the warp must take part.
+template <int n>
+__device__ __forceinline__ void lane_transpose(double (&x)[n], int l) {
+#pragma unroll
+    for (int M = n / 2; M >= 1; M /= 2) {
+        const bool hi = (l & M) != 0;
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+            if (p & M) continue;
+            const double send = hi ? x[p] : x[p | M];
+            const double r = __shfl_xor_sync(0xffffffffu, send, M);
+            if (hi) x[p] = r;
+            else x[p | M] = r;
+        }
+    }
 }
 
 template <int N>
@@ -127,7 +179,10 @@ __device__ __forceinline__ void pair_loop(const double* __restrict__ s, int base
     for (int i = 0; i < n; ++i) {
         const int ni = base + i * stride;
         const double hu_i = sHU[ni], hv_i = sHV[ni], u_i = sU[ni], v_i = sV[ni];
-        const double h_i = sH[ni], p_i = sP[ni];
+        const double h_i = sH[ni];
+        // 2g h_i (the per-pair pressure; the plane is absent with the shuffle hand-over)
+        double p_i = 0.0;
+        if constexpr (!vol_pressure_sums<N>()) p_i = sP[ni];
 #pragma unroll
         for (int q = i + 1; q < n; ++q) {
             const int nq = base + q * stride;
@@ -191,7 +246,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         S(F_HV)[idx] = hv;
         S(F_U)[idx] = u;
         S(F_V)[idx] = v;
-        S(F_P)[idx] = g2 * h;
+        if constexpr (!vol_shfl<N>()) S(F_P)[idx] = g2 * h;
     }
     __syncthreads();
 
@@ -215,8 +270,17 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
 #pragma unroll
     for (int p = 0; p < n; ++p) A1[p] = A2[p] = A3[p] = B2[p] = B3[p] = 0.0;
     if (valid) {
+        if constexpr (vol_shfl<N>()) {
+            // the pressure sums start from the source (see the eta-line)
+            // and run through both lines before they are scaled
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                B2[p] = m.ssx[k * nn + l * n + p];
+                B3[p] = m.ssy[k * nn + l * n + p];
+            }
+        }
         pair_loop<N, BLK>(sm, e * nn + l * n, 1, pmx, A1, A2, A3, B2, B3);
-        if constexpr (vol_pressure_sums<N>()) {
+        if constexpr (vol_pressure_sums<N>() && !vol_shfl<N>()) {
             // the pressure parts P Sx = 2g h_i h_q Sx: the node's 2g h times its sums
 #pragma unroll
             for (int p = 0; p < n; ++p) {
@@ -255,27 +319,45 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             }
         }
     }
+    if constexpr (vol_shfl<N>()) {
+        // row l -> column l of the element, on every lane of the warp
+        lane_transpose<n>(A1, l);
+        lane_transpose<n>(A2, l);
+        lane_transpose<n>(A3, l);
+        lane_transpose<n>(B2, l);
+        lane_transpose<n>(B3, l);
+    } else {
 #pragma unroll
-    for (int p = 0; p < n; ++p) {
-        S(F_A1)[e * nn + l * n + p] = A1[p];
-        S(F_A2)[e * nn + l * n + p] = A2[p];
-        S(F_A3)[e * nn + l * n + p] = A3[p];
+        for (int p = 0; p < n; ++p) {
+            S(F_A1)[e * nn + l * n + p] = A1[p];
+            S(F_A2)[e * nn + l * n + p] = A2[p];
+            S(F_A3)[e * nn + l * n + p] = A3[p];
+        }
+        __syncthreads();
+#pragma unroll
+        for (int p = 0; p < n; ++p) {
+            A1[p] = S(F_A1)[e * nn + p * n + l];
+            A2[p] = S(F_A2)[e * nn + p * n + l];
+            A3[p] = S(F_A3)[e * nn + p * n + l];
+        }
     }
-    __syncthreads();
 
     // ---- eta-line i = l, starting from the xi results ----------------------
-#pragma unroll
-    for (int p = 0; p < n; ++p) {
-        A1[p] = S(F_A1)[e * nn + p * n + l];
-        A2[p] = S(F_A2)[e * nn + p * n + l];
-        A3[p] = S(F_A3)[e * nn + p * n + l];
-    }
     if (valid) {
+        if constexpr (vol_pressure_sums<N>() && !vol_shfl<N>()) {
+            // the eta-line pressure sums start from the source: 2g h ssx
+            // scaled by f is the source term h srcx of the node
+#pragma unroll
+            for (int p = 0; p < n; ++p) {
+                B2[p] = m.ssx[k * nn + p * n + l];
+                B3[p] = m.ssy[k * nn + p * n + l];
+            }
+        }
         pair_loop<N, BLK>(sm, e * nn + l, n, pme, A1, A2, A3, B2, B3);
         if constexpr (vol_pressure_sums<N>()) {
 #pragma unroll
             for (int p = 0; p < n; ++p) {
-                const double pp = S(F_P)[e * nn + p * n + l];
+                const double pp = vol_shfl<N>() ? g2 * S(F_H)[e * nn + p * n + l] : S(F_P)[e * nn + p * n + l];
                 A2[p] = fma(pp, B2[p], A2[p]);
                 A3[p] = fma(pp, B3[p], A3[p]);
             }
@@ -297,7 +379,6 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
     // ---- nodes (i = l, j = p): lifts, viscous terms, source, scaling --------
     const int i = l;
     const double wi = wq<N>(i), wih = 0.5 * wi;
-    const int eb = e * nn;
 #pragma unroll
     for (int p = 0; p < n; ++p) {
         const int j = p;
@@ -336,10 +417,16 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             if (j == N) vlift(2, 1.0);
         }
         const double f = m.fwJ[gid];
-        const double h = S(F_H)[eb + j * n + i];
         a.R[gid] = m.fwJ2[gid] * a1;
-        a.R[m.KN + gid] = fma(h, m.srcx[gid], f * a2);
-        a.R[2 * m.KN + gid] = fma(h, m.srcy[gid], f * a3);
+        if constexpr (vol_pressure_sums<N>()) {
+            // the source is in the pressure sums
+            a.R[m.KN + gid] = f * a2;
+            a.R[2 * m.KN + gid] = f * a3;
+        } else {
+            const double h = S(F_H)[e * nn + j * n + i];
+            a.R[m.KN + gid] = fma(h, m.srcx[gid], f * a2);
+            a.R[2 * m.KN + gid] = fma(h, m.srcy[gid], f * a3);
+        }
     }
 }
 
