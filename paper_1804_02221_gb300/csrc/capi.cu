@@ -81,6 +81,11 @@ void free_all(swe_ctx* c) {
     c->allocations.clear();
     for (cudaEvent_t e : c->ev) cudaEventDestroy(e);
     c->ev.clear();
+    if (c->ev_fork) cudaEventDestroy(c->ev_fork);
+    if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->s_av) cudaStreamDestroy(c->s_av);
+    c->ev_fork = c->ev_join = nullptr;
+    c->s_av = nullptr;
 }
 
 }  // namespace
@@ -425,6 +430,10 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         W.vcount = static_cast<int*>(q);
         W.vlist = W.vcount + 4;
         cudaMemset(W.vcount, 0, sizeof(int) * ((size_t)K + 4));
+        e2 = cudaStreamCreateWithFlags(&c->s_av, cudaStreamNonBlocking);
+        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+        if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: stream"); }
     }
     if (!shared_status) cudaMemset(W.status, 0, sizeof(int));
     swe::prepare_volume(c);
@@ -462,13 +471,33 @@ extern "C" void swe_destroy(swe_ctx* c) {
 
 namespace swe {
 
+// The interface flux on s and, with AV, the smoothness indicator on the
+// context's second stream: both read only W and its velocities. After the
+// join: extra(s) (the viscous time step of a step's first stage, which needs
+// the viscosities), then the viscous fluxes (which read the BR1 interface
+// values of the interface-flux kernel) and the viscous interface average.
+// Fork and join are events, so the pair also runs inside a stream capture.
+template <typename F>
+void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, F extra) {
+    if (c->p.av) {
+        cudaEventRecord(c->ev_fork, s);
+        cudaStreamWaitEvent(c->s_av, c->ev_fork, 0);
+        launch_indicator(c, W, c->s_av, stop);
+        cudaEventRecord(c->ev_join, c->s_av);
+        launch_surface(c, W, s, stop);
+        cudaStreamWaitEvent(s, c->ev_join, 0);
+        extra(s);
+        launch_visc_flux(c, W, s, stop);
+        launch_visc_face(c, s, stop);
+    } else {
+        launch_surface(c, W, s, stop);
+        extra(s);
+    }
+}
+
 void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done) {
     if (!prim_done) launch_prim(c, W, s, stop);
-    launch_surface(c, W, s, stop);
-    if (c->p.av) {
-        launch_av(c, W, s, stop);
-        launch_visc_face(c, s, stop);
-    }
+    fluxes_and_viscosity(c, W, s, stop, [](cudaStream_t) {});
     launch_volume(c, W, R, s, stop);
 }
 
@@ -484,10 +513,7 @@ void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int stage = 0; stage < stages; ++stage) {
         if (stage == 0 && visc_dt) {
-            launch_surface(c, W, s, stop);
-            launch_av(c, W, s, stop);
-            launch_dt(c, W, 0.0, s, stop);
-            launch_visc_face(c, s, stop);
+            fluxes_and_viscosity(c, W, s, stop, [&](cudaStream_t st) { launch_dt(c, W, 0.0, st, stop); });
             launch_volume(c, W, c->w.R, s, stop);
         } else {
             rhs_chain(c, W, c->w.R, s, stop, true);
@@ -530,10 +556,7 @@ extern "C" int swe_max_dt(swe_ctx* c, const double* W, double* dt_cfl, double* d
     if (!c || !W) return fail(SWE_ERR_ARG, "swe_max_dt: NULL argument");
     cudaStream_t s = (cudaStream_t)stream;
     swe::launch_prim(c, W, s, nullptr);
-    if (c->kv > 0.0) {  // the element viscosities of W for the viscous restriction
-        swe::launch_surface(c, W, s, nullptr);
-        swe::launch_av(c, W, s, nullptr);
-    }
+    if (c->kv > 0.0) swe::launch_indicator(c, W, s, nullptr);  // the element viscosities of W (viscous restriction)
     swe::launch_dt(c, W, 0.0, s, nullptr);
     double h[4];
     cudaMemcpyAsync(h, c->w.dt, 3 * sizeof(double), cudaMemcpyDeviceToHost, s);

@@ -231,10 +231,7 @@ extern "C" int swe_ens_max_dt(swe_ens* e, const double* W, double* dt_cfl, doubl
     for (size_t gi = 0; gi < e->groups.size(); ++gi) {
         swe_ctx* c = e->groups[gi];
         swe::launch_prim(c, W + e->goff[gi], s, nullptr);
-        if (c->kv > 0.0) {  // the element viscosities for the viscous restriction
-            swe::launch_surface(c, W + e->goff[gi], s, nullptr);
-            swe::launch_av(c, W + e->goff[gi], s, nullptr);
-        }
+        if (c->kv > 0.0) swe::launch_indicator(c, W + e->goff[gi], s, nullptr);  // viscosities (viscous restriction)
         swe::launch_dt(c, W + e->goff[gi], 0.0, s, nullptr);
     }
     e->launches += sum_launches(e) - before;

@@ -316,16 +316,18 @@ __global__ void __launch_bounds__(vf_threads<N>()) k_visc_flux(AvArgs a) {
 }
 
 template <int N>
-void av_n(swe_ctx* c, const AvArgs& a, cudaStream_t s) {
+void indicator_n(swe_ctx* c, const AvArgs& a, cudaStream_t s) {
     cudaMemsetAsync(a.vcount, 0, sizeof(int), s);
-    {
-        // the wide mapping when it still gives at least 8 warps per SM
-        const bool wide = c->m.K >= (long long)av_epw<N, true>() * 8 * c->sms;
-        const int blocks = grid_for(c->m.K, AV_WPB * (wide ? av_epw<N, true>() : av_epw<N, false>()));
-        Timed tm(c, KC_AV, s);
-        if (wide) k_av<N, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
-        else k_av<N, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
-    }
+    // the wide mapping when it still gives at least 8 warps per SM
+    const bool wide = c->m.K >= (long long)av_epw<N, true>() * 8 * c->sms;
+    const int blocks = grid_for(c->m.K, AV_WPB * (wide ? av_epw<N, true>() : av_epw<N, false>()));
+    Timed tm(c, KC_AV, s);
+    if (wide) k_av<N, true><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+    else k_av<N, false><<<blocks, 32 * AV_WPB, 0, s>>>(a);
+}
+
+template <int N>
+void visc_flux_n(swe_ctx* c, const AvArgs& a, cudaStream_t s) {
     // blocks striding over the list of viscous elements: at most one group of
     // EB elements per block per pass, eight blocks per SM
     const int groups = grid_for(c->m.K, vf_eb<N>());
@@ -349,24 +351,49 @@ EpsParams eps_params(const swe_ctx* c) {
     return EpsParams{c->p.eps0, c->sigma_min, c->sigma_max, pow(10.0, c->sigma_min), pow(10.0, c->sigma_max)};
 }
 
-void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
+void launch_indicator(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
     AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.Lv, c->w.eps, c->w.vlist, c->w.vcount,
              eps_params(c), stop};
     switch (c->m.N) {
-        case 1: av_n<1>(c, a, s); break;
-        case 2: av_n<2>(c, a, s); break;
-        case 3: av_n<3>(c, a, s); break;
-        case 4: av_n<4>(c, a, s); break;
-        case 5: av_n<5>(c, a, s); break;
-        case 6: av_n<6>(c, a, s); break;
-        case 7: av_n<7>(c, a, s); break;
-        case 8: av_n<8>(c, a, s); break;
-        case 9: av_n<9>(c, a, s); break;
-        case 10: av_n<10>(c, a, s); break;
-        case 11: av_n<11>(c, a, s); break;
-        case 12: av_n<12>(c, a, s); break;
+        case 1: indicator_n<1>(c, a, s); break;
+        case 2: indicator_n<2>(c, a, s); break;
+        case 3: indicator_n<3>(c, a, s); break;
+        case 4: indicator_n<4>(c, a, s); break;
+        case 5: indicator_n<5>(c, a, s); break;
+        case 6: indicator_n<6>(c, a, s); break;
+        case 7: indicator_n<7>(c, a, s); break;
+        case 8: indicator_n<8>(c, a, s); break;
+        case 9: indicator_n<9>(c, a, s); break;
+        case 10: indicator_n<10>(c, a, s); break;
+        case 11: indicator_n<11>(c, a, s); break;
+        case 12: indicator_n<12>(c, a, s); break;
         default: break;
     }
+}
+
+void launch_visc_flux(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
+    AvArgs a{c->m, W, c->w.uv, c->w.Ustar, c->w.Fvt, c->w.Fvtr, c->w.Lv, c->w.eps, c->w.vlist, c->w.vcount,
+             eps_params(c), stop};
+    switch (c->m.N) {
+        case 1: visc_flux_n<1>(c, a, s); break;
+        case 2: visc_flux_n<2>(c, a, s); break;
+        case 3: visc_flux_n<3>(c, a, s); break;
+        case 4: visc_flux_n<4>(c, a, s); break;
+        case 5: visc_flux_n<5>(c, a, s); break;
+        case 6: visc_flux_n<6>(c, a, s); break;
+        case 7: visc_flux_n<7>(c, a, s); break;
+        case 8: visc_flux_n<8>(c, a, s); break;
+        case 9: visc_flux_n<9>(c, a, s); break;
+        case 10: visc_flux_n<10>(c, a, s); break;
+        case 11: visc_flux_n<11>(c, a, s); break;
+        case 12: visc_flux_n<12>(c, a, s); break;
+        default: break;
+    }
+}
+
+void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop) {
+    launch_indicator(c, W, s, stop);
+    launch_visc_flux(c, W, s, stop);
 }
 
 }  // namespace swe

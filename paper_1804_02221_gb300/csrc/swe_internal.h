@@ -194,6 +194,11 @@ struct swe_ctx {
     // launch shapes (swe_autotune): volume threads per block, update warps per block
     int vol_tpb = 128;
     int upd_wpb = 4;
+    // the smoothness indicator of a right-hand side runs on this second
+    // stream beside the interface flux, forked from and joined back into the
+    // caller's stream by the two events (null without artificial viscosity)
+    cudaStream_t s_av = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // viscous time-step factor kv = (N+1)^3 cfl / (8 cfl_visc); 0 = the paper's rule
     double kv = 0.0;
     // timing: on, and the kernel classes whose launches get events (bit c = class c)
@@ -237,8 +242,12 @@ void launch_surface(swe_ctx* c, const double* W, cudaStream_t s, const int* stop
 void launch_volume(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
 void launch_volume_std(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop);
 EpsParams eps_params(const swe_ctx* c);
-// The element viscosities of W (indicator), and for the viscous elements the
-// BR1 gradients, viscous fluxes and the volume part of their divergence.
+// The element viscosities of W and the list of viscous elements (indicator).
+void launch_indicator(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+// For the listed viscous elements: the BR1 gradients (from the interface
+// values in w.Ustar), viscous fluxes and the volume part of their divergence.
+void launch_visc_flux(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
+// Both of the above.
 void launch_av(swe_ctx* c, const double* W, cudaStream_t s, const int* stop);
 // The list of viscous elements (w.vlist, w.vcount) from the viscosities in w.eps.
 void launch_visc_list(swe_ctx* c, cudaStream_t s);
