@@ -83,8 +83,9 @@ void free_all(swe_ctx* c) {
     c->ev.clear();
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
+    if (c->ev_dt) cudaEventDestroy(c->ev_dt);
     if (c->s_av) cudaStreamDestroy(c->s_av);
-    c->ev_fork = c->ev_join = nullptr;
+    c->ev_fork = c->ev_join = c->ev_dt = nullptr;
     c->s_av = nullptr;
 }
 
@@ -430,11 +431,12 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         W.vcount = static_cast<int*>(q);
         W.vlist = W.vcount + 4;
         cudaMemset(W.vcount, 0, sizeof(int) * ((size_t)K + 4));
-        e2 = cudaStreamCreateWithFlags(&c->s_av, cudaStreamNonBlocking);
-        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-        if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: stream"); }
     }
+    e2 = cudaStreamCreateWithFlags(&c->s_av, cudaStreamNonBlocking);
+    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_dt, cudaEventDisableTiming);
+    if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: stream"); }
     if (!shared_status) cudaMemset(W.status, 0, sizeof(int));
     swe::prepare_volume(c);
     cudaMemset(W.eps, 0, sizeof(double) * K);
@@ -473,48 +475,54 @@ namespace swe {
 
 // The interface flux on s and, with AV, the smoothness indicator on the
 // context's second stream: both read only W and its velocities. After the
-// join: extra(s) (the viscous time step of a step's first stage, which needs
-// the viscosities), then the viscous fluxes (which read the BR1 interface
-// values of the interface-flux kernel) and the viscous interface average.
-// Fork and join are events, so the pair also runs inside a stream capture.
-template <typename F>
-void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, F extra) {
-    if (c->p.av) {
+// join, on s, the viscous fluxes (which read the BR1 interface values of the
+// interface-flux kernel) and the viscous interface average. With dt_side,
+// the time step of W follows the indicator on the second stream (the
+// viscous restriction reads its viscosities) and ev_dt marks its end: the
+// caller makes s wait for it before the first stage update. Fork and joins
+// are events, so all of it also runs inside a stream capture.
+void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool dt_side) {
+    if (c->p.av || dt_side) {
         cudaEventRecord(c->ev_fork, s);
         cudaStreamWaitEvent(c->s_av, c->ev_fork, 0);
+    }
+    if (c->p.av) {
         launch_indicator(c, W, c->s_av, stop);
         cudaEventRecord(c->ev_join, c->s_av);
-        launch_surface(c, W, s, stop);
+    }
+    if (dt_side) {
+        launch_dt(c, W, 0.0, c->s_av, stop);
+        cudaEventRecord(c->ev_dt, c->s_av);
+    }
+    launch_surface(c, W, s, stop);
+    if (c->p.av) {
         cudaStreamWaitEvent(s, c->ev_join, 0);
-        extra(s);
         launch_visc_flux(c, W, s, stop);
         launch_visc_face(c, s, stop);
-    } else {
-        launch_surface(c, W, s, stop);
-        extra(s);
     }
 }
 
 void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done) {
     if (!prim_done) launch_prim(c, W, s, stop);
-    fluxes_and_viscosity(c, W, s, stop, [](cudaStream_t) {});
+    fluxes_and_viscosity(c, W, s, stop, false);
     launch_volume(c, W, R, s, stop);
 }
 
 void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop, bool save) {
     const bool adaptive = !(dt > 0.0);
     const double* dtd = adaptive ? c->w.dt : nullptr;
-    // the viscous restriction needs eps of the step's start state: the time
-    // step then runs after the first stage's AV kernel (which computes it)
-    const bool visc_dt = adaptive && c->kv > 0.0;
     if (save) launch_copy(c, W, c->w.Wn, 3 * c->m.KN, s, stop);
-    if (adaptive && !visc_dt) launch_dt(c, W, 0.0, s, stop);
     const int stages = c->p.rk == 0 ? 5 : 3;
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int stage = 0; stage < stages; ++stage) {
-        if (stage == 0 && visc_dt) {
-            fluxes_and_viscosity(c, W, s, stop, [&](cudaStream_t st) { launch_dt(c, W, 0.0, st, stop); });
+        if (stage == 0 && adaptive) {
+            // the time step of the start state runs on the second stream
+            // beside the first right-hand side (after the indicator, whose
+            // viscosities the viscous restriction reads); the first stage
+            // update is the first reader of dt
+            fluxes_and_viscosity(c, W, s, stop, true);
             launch_volume(c, W, c->w.R, s, stop);
+            cudaStreamWaitEvent(s, c->ev_dt, 0);
         } else {
             rhs_chain(c, W, c->w.R, s, stop, true);
         }

@@ -194,11 +194,12 @@ struct swe_ctx {
     // launch shapes (swe_autotune): volume threads per block, update warps per block
     int vol_tpb = 128;
     int upd_wpb = 4;
-    // the smoothness indicator of a right-hand side runs on this second
-    // stream beside the interface flux, forked from and joined back into the
-    // caller's stream by the two events (null without artificial viscosity)
+    // the smoothness indicator of a right-hand side (and a step's time step)
+    // run on this second stream beside the interface flux, forked from the
+    // caller's stream by ev_fork and joined back by ev_join (indicator) and
+    // ev_dt (time step)
     cudaStream_t s_av = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dt = nullptr;
     // viscous time-step factor kv = (N+1)^3 cfl / (8 cfl_visc); 0 = the paper's rule
     double kv = 0.0;
     // timing: on, and the kernel classes whose launches get events (bit c = class c)
