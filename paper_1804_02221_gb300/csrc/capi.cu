@@ -83,9 +83,9 @@ void free_all(swe_ctx* c) {
     c->ev.clear();
     if (c->ev_fork) cudaEventDestroy(c->ev_fork);
     if (c->ev_join) cudaEventDestroy(c->ev_join);
-    if (c->ev_dt) cudaEventDestroy(c->ev_dt);
+    if (c->ev_first) cudaEventDestroy(c->ev_first);
     if (c->s_av) cudaStreamDestroy(c->s_av);
-    c->ev_fork = c->ev_join = c->ev_dt = nullptr;
+    c->ev_fork = c->ev_join = c->ev_first = nullptr;
     c->s_av = nullptr;
 }
 
@@ -435,7 +435,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
     e2 = cudaStreamCreateWithFlags(&c->s_av, cudaStreamNonBlocking);
     if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
     if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_dt, cudaEventDisableTiming);
+    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_first, cudaEventDisableTiming);
     if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: stream"); }
     if (!shared_status) cudaMemset(W.status, 0, sizeof(int));
     swe::prepare_volume(c);
@@ -476,13 +476,16 @@ namespace swe {
 // The interface flux on s and, with AV, the smoothness indicator on the
 // context's second stream: both read only W and its velocities. After the
 // join, on s, the viscous fluxes (which read the BR1 interface values of the
-// interface-flux kernel) and the viscous interface average. With dt_side,
-// the time step of W follows the indicator on the second stream (the
-// viscous restriction reads its viscosities) and ev_dt marks its end: the
-// caller makes s wait for it before the first stage update. Fork and joins
-// are events, so all of it also runs inside a stream capture.
-void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool dt_side) {
-    if (c->p.av || dt_side) {
+// interface-flux kernel) and the viscous interface average. A step's first
+// right-hand side also puts the step's own work on the second stream, after
+// the indicator: the copy of the start state (save, for the rollback of a
+// failed step) and the time step of W (dt_side; the viscous restriction
+// reads the indicator's viscosities). ev_first marks its end, and the caller
+// makes s wait for it before the first stage update, the first writer of W
+// and reader of dt. Fork and joins are events, so all of it also runs
+// inside a stream capture.
+void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool save, bool dt_side) {
+    if (c->p.av || save || dt_side) {
         cudaEventRecord(c->ev_fork, s);
         cudaStreamWaitEvent(c->s_av, c->ev_fork, 0);
     }
@@ -490,10 +493,9 @@ void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int
         launch_indicator(c, W, c->s_av, stop);
         cudaEventRecord(c->ev_join, c->s_av);
     }
-    if (dt_side) {
-        launch_dt(c, W, 0.0, c->s_av, stop);
-        cudaEventRecord(c->ev_dt, c->s_av);
-    }
+    if (save) launch_copy(c, W, c->w.Wn, 3 * c->m.KN, c->s_av, stop);
+    if (dt_side) launch_dt(c, W, 0.0, c->s_av, stop);
+    if (save || dt_side) cudaEventRecord(c->ev_first, c->s_av);
     launch_surface(c, W, s, stop);
     if (c->p.av) {
         cudaStreamWaitEvent(s, c->ev_join, 0);
@@ -504,30 +506,28 @@ void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int
 
 void rhs_chain(swe_ctx* c, const double* W, double* R, cudaStream_t s, const int* stop, bool prim_done) {
     if (!prim_done) launch_prim(c, W, s, stop);
-    fluxes_and_viscosity(c, W, s, stop, false);
+    fluxes_and_viscosity(c, W, s, stop, false, false);
     launch_volume(c, W, R, s, stop);
 }
 
 void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop, bool save) {
     const bool adaptive = !(dt > 0.0);
     const double* dtd = adaptive ? c->w.dt : nullptr;
-    if (save) launch_copy(c, W, c->w.Wn, 3 * c->m.KN, s, stop);
     const int stages = c->p.rk == 0 ? 5 : 3;
     const double ca[3] = {0.0, 0.75, 1.0 / 3.0}, cb[3] = {1.0, 0.25, 2.0 / 3.0};
     for (int stage = 0; stage < stages; ++stage) {
-        if (stage == 0 && adaptive) {
-            // the time step of the start state runs on the second stream
-            // beside the first right-hand side (after the indicator, whose
-            // viscosities the viscous restriction reads); the first stage
-            // update is the first reader of dt
-            fluxes_and_viscosity(c, W, s, stop, true);
+        if (stage == 0 && (adaptive || save)) {
+            // the copy of the start state and its time step run on the
+            // second stream beside the first right-hand side; the first
+            // stage update waits for them
+            fluxes_and_viscosity(c, W, s, stop, save, adaptive);
             launch_volume(c, W, c->w.R, s, stop);
-            cudaStreamWaitEvent(s, c->ev_dt, 0);
+            cudaStreamWaitEvent(s, c->ev_first, 0);
         } else {
             rhs_chain(c, W, c->w.R, s, stop, true);
         }
         if (c->p.rk == 0)
-            launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop, true);
+            launch_update(c, 1, W, kLsrkA[stage], kLsrkB[stage], dt, dtd, s, stop, true, stage + 1 < stages);
         else
             launch_update(c, 2, W, ca[stage], cb[stage], dt, dtd, s, stop, true);
     }

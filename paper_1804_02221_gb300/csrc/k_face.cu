@@ -241,6 +241,7 @@ struct UpdArgs {
     double* W;
     const double* R;
     double* Kreg;
+    int wreg;  // write the register (0 at a scheme's last stage: nothing reads it there)
     const double* Wn;
     double a, b, dt_host;
     const double* dt_dev;
@@ -355,9 +356,11 @@ __device__ __forceinline__ void update_element(const UpdArgs& a, long long k, bo
                     k1v = fma(a.a, a.Kreg[KN + gid], k1v);
                     k2v = fma(a.a, a.Kreg[2 * KN + gid], k2v);
                 }
-                a.Kreg[gid] = k0v;
-                a.Kreg[KN + gid] = k1v;
-                a.Kreg[2 * KN + gid] = k2v;
+                if (a.wreg) {
+                    a.Kreg[gid] = k0v;
+                    a.Kreg[KN + gid] = k1v;
+                    a.Kreg[2 * KN + gid] = k2v;
+                }
                 w0 = fma(bdt, k0v, w0);
                 w1 = fma(bdt, k1v, w1);
                 w2 = fma(bdt, k2v, w2);
@@ -812,8 +815,8 @@ void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop) {
 }
 
 void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,
-                   const double* dt_dev, cudaStream_t s, const int* stop, bool write_uv) {
-    UpdArgs u{c->m, W, c->w.R, c->w.Kreg, c->w.Wn, a, b, dt_host, dt_dev, c->p.limiter,
+                   const double* dt_dev, cudaStream_t s, const int* stop, bool write_uv, bool write_reg) {
+    UpdArgs u{c->m, W, c->w.R, c->w.Kreg, write_reg ? 1 : 0, c->w.Wn, a, b, dt_host, dt_dev, c->p.limiter,
               c->h_tol, write_uv ? c->w.uv : nullptr, c->w.status, stop};
 #define SWE_UPD(NN) update_n<NN>(c, mode, u, s)
     SWE_SWITCH_N(c->m.N, SWE_UPD)

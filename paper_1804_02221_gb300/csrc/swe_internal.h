@@ -194,12 +194,13 @@ struct swe_ctx {
     // launch shapes (swe_autotune): volume threads per block, update warps per block
     int vol_tpb = 128;
     int upd_wpb = 4;
-    // the smoothness indicator of a right-hand side (and a step's time step)
-    // run on this second stream beside the interface flux, forked from the
-    // caller's stream by ev_fork and joined back by ev_join (indicator) and
-    // ev_dt (time step)
+    // the smoothness indicator of a right-hand side (and a step's copy of its
+    // start state and its time step) run on this second stream beside the
+    // interface flux, forked from the caller's stream by ev_fork and joined
+    // back by ev_join (indicator) and ev_first (copy and time step, before
+    // the first stage update)
     cudaStream_t s_av = nullptr;
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_dt = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_first = nullptr;
     // viscous time-step factor kv = (N+1)^3 cfl / (8 cfl_visc); 0 = the paper's rule
     double kv = 0.0;
     // timing: on, and the kernel classes whose launches get events (bit c = class c)
@@ -256,9 +257,10 @@ void launch_visc_face(swe_ctx* c, cudaStream_t s, const int* stop);
 void launch_ustar(swe_ctx* c, cudaStream_t s);
 // mode 0: limiter only; 1: 2N-storage stage Kh = a Kh + R, W += (b dt) Kh
 // (the register holds K/dt); 2: SSP stage W = a Wn + b (W + dt R).
-// write_uv: also write the velocities of the new state into the work buffer.
+// write_uv: also write the velocities of the new state into the work buffer;
+// write_reg (mode 1): store the register (not needed after the last stage).
 void launch_update(swe_ctx* c, int mode, double* W, double a, double b, double dt_host,
-                   const double* dt_dev, cudaStream_t s, const int* stop, bool write_uv);
+                   const double* dt_dev, cudaStream_t s, const int* stop, bool write_uv, bool write_reg = true);
 void launch_dt(swe_ctx* c, const double* W, double dt_fixed, cudaStream_t s, const int* stop);
 void launch_copy(swe_ctx* c, const double* src, double* dst, long long count, cudaStream_t s,
                  const int* stop);
