@@ -432,11 +432,14 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         W.vlist = W.vcount + 4;
         cudaMemset(W.vcount, 0, sizeof(int) * ((size_t)K + 4));
     }
-    e2 = cudaStreamCreateWithFlags(&c->s_av, cudaStreamNonBlocking);
-    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
-    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
-    if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_first, cudaEventDisableTiming);
-    if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: stream"); }
+    c->side = KN >= (1LL << 20);
+    if (c->side) {
+        e2 = cudaStreamCreateWithFlags(&c->s_av, cudaStreamNonBlocking);
+        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_fork, cudaEventDisableTiming);
+        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_join, cudaEventDisableTiming);
+        if (e2 == cudaSuccess) e2 = cudaEventCreateWithFlags(&c->ev_first, cudaEventDisableTiming);
+        if (e2 != cudaSuccess) { free_all(c); delete c; return cuda_fail(e2, "swe_create: stream"); }
+    }
     if (!shared_status) cudaMemset(W.status, 0, sizeof(int));
     swe::prepare_volume(c);
     cudaMemset(W.eps, 0, sizeof(double) * K);
@@ -484,21 +487,24 @@ namespace swe {
 // makes s wait for it before the first stage update, the first writer of W
 // and reader of dt. Fork and joins are events, so all of it also runs
 // inside a stream capture.
+// Without c->side everything runs on s in the same order (same results).
 void fluxes_and_viscosity(swe_ctx* c, const double* W, cudaStream_t s, const int* stop, bool save, bool dt_side) {
-    if (c->p.av || save || dt_side) {
+    const bool fork = c->side && (c->p.av || save || dt_side);
+    cudaStream_t t = fork ? c->s_av : s;
+    if (fork) {
         cudaEventRecord(c->ev_fork, s);
-        cudaStreamWaitEvent(c->s_av, c->ev_fork, 0);
+        cudaStreamWaitEvent(t, c->ev_fork, 0);
     }
     if (c->p.av) {
-        launch_indicator(c, W, c->s_av, stop);
-        cudaEventRecord(c->ev_join, c->s_av);
+        launch_indicator(c, W, t, stop);
+        if (fork) cudaEventRecord(c->ev_join, t);
     }
-    if (save) launch_copy(c, W, c->w.Wn, 3 * c->m.KN, c->s_av, stop);
-    if (dt_side) launch_dt(c, W, 0.0, c->s_av, stop);
-    if (save || dt_side) cudaEventRecord(c->ev_first, c->s_av);
+    if (save) launch_copy(c, W, c->w.Wn, 3 * c->m.KN, t, stop);
+    if (dt_side) launch_dt(c, W, 0.0, t, stop);
+    if (fork && (save || dt_side)) cudaEventRecord(c->ev_first, t);
     launch_surface(c, W, s, stop);
     if (c->p.av) {
-        cudaStreamWaitEvent(s, c->ev_join, 0);
+        if (fork) cudaStreamWaitEvent(s, c->ev_join, 0);
         launch_visc_flux(c, W, s, stop);
         launch_visc_face(c, s, stop);
     }
@@ -522,7 +528,7 @@ void step_once(swe_ctx* c, double* W, double dt, cudaStream_t s, const int* stop
             // stage update waits for them
             fluxes_and_viscosity(c, W, s, stop, save, adaptive);
             launch_volume(c, W, c->w.R, s, stop);
-            cudaStreamWaitEvent(s, c->ev_first, 0);
+            if (c->side) cudaStreamWaitEvent(s, c->ev_first, 0);
         } else {
             rhs_chain(c, W, c->w.R, s, stop, true);
         }

@@ -85,22 +85,24 @@ constexpr bool vol_pressure_sums() {
 }
 
 // The xi -> eta hand-over through warp shuffles. Where n = N + 1 is a power
-// of two (N = 7 of the built degrees), every element's n lines are n
-// consecutive lanes of one warp, and the hand-over is an n x n transpose of
-// each accumulator across those lanes. The pressure sums then travel with
-// the other accumulators unscaled and are scaled by 2g h once per node, after
-// the eta-line (2 FP64 instructions per node fewer); the block stages only
-// the five state planes and needs no second barrier.
+// of two (N = 3 and 7 of the line kernel's degrees), every element's n lines
+// are n consecutive lanes of one warp, and the hand-over is an n x n
+// transpose of each accumulator across those lanes: the block needs no
+// hand-over planes and no second barrier. With the pressure sums (N = 7)
+// the sums travel with the other accumulators unscaled and are scaled by
+// 2g h once per node, after the eta-line (2 FP64 instructions per node
+// fewer), and the block stages only the five state planes.
 template <int N>
 constexpr bool vol_shfl() {
-    return vol_pressure_sums<N>() && ((N + 1) & N) == 0 && N + 1 <= 32;
+    return ((N + 1) & N) == 0 && N + 1 <= 32;
 }
 
-// Shared-memory planes: the staged state (and 2g h, and the hand-over
-// planes, where the hand-over goes through shared memory).
+// Shared-memory planes: the staged state, 2g h where the pairs form the
+// pressure, and the hand-over planes where the hand-over goes through
+// shared memory.
 template <int N>
 constexpr int vol_planes() {
-    return vol_shfl<N>() ? (int)F_P : (int)F_COUNT;
+    return vol_shfl<N>() ? (vol_pressure_sums<N>() ? (int)F_P : (int)F_P + 1) : (int)F_COUNT;
 }
 
 template <int N, bool AV, int TPB>
@@ -118,18 +120,19 @@ constexpr bool vol_fits() {
 // Blocks per SM that the shared memory admits (228 KB per SM, 1 KB reserved
 // per block), passed to __launch_bounds__ so that the register allocation
 // does not lower the occupancy below what the staging allows.
-// With the shuffle hand-over the staging admits more blocks than the
-// registers of the pair loops allow; there the bound keeps 168 registers a
-// thread (the budget of the shared-memory hand-over at N = 7).
+// The bound is the block count that the staging of the shared-memory
+// hand-over (all F_COUNT planes) admits, also where the shuffle hand-over
+// stages fewer planes: the shuffle variants keep the registers of the pair
+// loops (168 a thread at N = 7; capping them to the blocks the smaller
+// staging admits spills).
 template <int N, bool AV, int TPB>
 constexpr int vol_min_blocks() {
     constexpr int threads = vol_ne<N, TPB>() * (N + 1);
     constexpr int warps = (threads + 31) / 32;
-    constexpr int by_smem = (int)((228 * 1024) / (vol_smem<N, AV, TPB>() + 1024));
+    constexpr size_t full = sizeof(double) * ((size_t)F_COUNT * vol_ne<N, TPB>() * (N + 1) * (N + 1));
+    constexpr int by_smem = (int)((228 * 1024) / (full + 1024));
     constexpr int by_warps = 64 / warps;
-    constexpr int by_regs = vol_shfl<N>() ? 65536 / (threads * 168) : 64;
-    constexpr int b0 = by_smem < by_warps ? by_smem : by_warps;
-    constexpr int b = b0 < by_regs ? b0 : by_regs;
+    constexpr int b = by_smem < by_warps ? by_smem : by_warps;
     return b > 0 ? b : 1;
 }
 
@@ -246,7 +249,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         S(F_HV)[idx] = hv;
         S(F_U)[idx] = u;
         S(F_V)[idx] = v;
-        if constexpr (!vol_shfl<N>()) S(F_P)[idx] = g2 * h;
+        if constexpr (vol_planes<N>() > (int)F_P) S(F_P)[idx] = g2 * h;
     }
     __syncthreads();
 
@@ -270,7 +273,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
 #pragma unroll
     for (int p = 0; p < n; ++p) A1[p] = A2[p] = A3[p] = B2[p] = B3[p] = 0.0;
     if (valid) {
-        if constexpr (vol_shfl<N>()) {
+        if constexpr (vol_shfl<N>() && vol_pressure_sums<N>()) {
             // the pressure sums start from the source (see the eta-line)
             // and run through both lines before they are scaled
 #pragma unroll
@@ -324,8 +327,10 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         lane_transpose<n>(A1, l);
         lane_transpose<n>(A2, l);
         lane_transpose<n>(A3, l);
-        lane_transpose<n>(B2, l);
-        lane_transpose<n>(B3, l);
+        if constexpr (vol_pressure_sums<N>()) {
+            lane_transpose<n>(B2, l);
+            lane_transpose<n>(B3, l);
+        }
     } else {
 #pragma unroll
         for (int p = 0; p < n; ++p) {

@@ -198,7 +198,10 @@ struct swe_ctx {
     // start state and its time step) run on this second stream beside the
     // interface flux, forked from the caller's stream by ev_fork and joined
     // back by ev_join (indicator) and ev_first (copy and time step, before
-    // the first stage update)
+    // the first stage update); only on meshes of at least 2^20 nodes (side):
+    // on smaller ones the launches, not the kernels, set the pace, and the
+    // fork and joins cost more than the overlap gains
+    bool side = false;
     cudaStream_t s_av = nullptr;
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr, ev_first = nullptr;
     // viscous time-step factor kv = (N+1)^3 cfl / (8 cfl_visc); 0 = the paper's rule
