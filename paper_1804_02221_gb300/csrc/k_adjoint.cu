@@ -1083,6 +1083,18 @@ void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* W
     if (av) vol_adj_n<NN, true>(c, va, s); else vol_adj_n<NN, false>(c, va, s)
     SWE_SWITCH_N_ADJ(m.N, SWE_VA)
 #undef SWE_VA
+    // The source coefficients onto b read only the volume kernel's Gsrc: on
+    // large meshes they run on the second stream beside the viscous and
+    // interface-flux reverse kernels, and the gather (the other writer of
+    // bbar) waits for them.
+    const bool src_now = bbar && !defer_src;
+    const bool src_side = src_now && c->side;
+    if (src_side) {
+        cudaEventRecord(c->ev_fork, s);
+        cudaStreamWaitEvent(c->s_av, c->ev_fork, 0);
+        launch_src_adjoint(c, A.Gsrc, bbar, c->s_av);
+        cudaEventRecord(c->ev_join, c->s_av);
+    }
     if (av) {
         const long long total = (long long)m.nfaces * m.n;
         if (total > 0) {
@@ -1120,6 +1132,7 @@ void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* W
                 k_wall_adj<false><<<grid_for(walls, 128), 128, 0, s>>>(m, W, c->w.uv, A.Gfo, A.GUs, av, A.Gsl);
         }
     }
+    if (src_side) cudaStreamWaitEvent(s, c->ev_join, 0);
     GatherArgs ga{m, W, c->w.uv, A.Ga, A.Guv, A.Gsl, Wbar, bbar};
 #define SWE_GA(NN)                                                                          \
     {                                                                                       \
@@ -1128,7 +1141,7 @@ void launch_rhs_adjoint(swe_ctx* c, const double* W, const double* Rb, double* W
     }
     SWE_SWITCH_N_ADJ(m.N, SWE_GA)
 #undef SWE_GA
-    if (bbar && !defer_src) launch_src_adjoint(c, A.Gsrc, bbar, s);
+    if (src_now && !src_side) launch_src_adjoint(c, A.Gsrc, bbar, s);
 }
 
 void launch_src_adjoint(swe_ctx* c, const double* Gsrc, double* bbar, cudaStream_t s) {

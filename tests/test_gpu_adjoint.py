@@ -43,6 +43,9 @@ CASES = [
     ("dry_n3", lambda: I.random_rough(N=3, K1=4, seed=7, dry_fraction=0.2), dict(flux=1, av=True, **AV)),
     # viscous elements next to inviscid ones, nearly dry nodes at a wet/dry front
     ("thacker_front", lambda: I.thacker_bowl(N=3, K1=8), dict(flux=1, av=True, eps0=0.01)),
+    # 2^20 nodes: a context this large runs the source coefficients onto b on
+    # its second stream, beside the reverse interface flux and viscosity
+    ("dam_break_2p20", lambda: I.dam_break(N=7, K1=128), dict(flux=1, av=True, eps0=0.025)),
 ]
 
 
