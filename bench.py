@@ -543,6 +543,15 @@ def adjoint_bench(args):
     Wb, bb = torch.zeros_like(W0), torch.zeros_like(W0[0])
     ms_rhs_adj, _ = timed(lambda: [ctx.rhs_adjoint(W0, Rbar, Wb, bb) for _ in range(20)])
     nodes = p.nodes
+    # launch shapes on this mesh (4096 elements: 164 blocks of the default
+    # 128-thread volume shape for 152 SMs): the tuner's choice against the
+    # defaults, on the plain forward path and one right-hand side
+    ctx.autotune(W0)
+    tuned = ctx.tuning()
+    W = W0.clone()
+    ms_plain_t, _ = timed(lambda: [ctx.step(W, dt, 1) for dt in run.dts])
+    ms_rhs_t, _ = timed(lambda: [ctx.rhs(W0, R) for _ in range(20)])
+    ctx.set_tuning(128, 4)
     # one right-hand side and its adjoint at the main workload's size (N=7, 4.19M nodes)
     big = I.dam_break(N=7)
     cb = swedg.SweContext.from_problem(big, flux=1, av=True, eps0=0.025)
@@ -591,6 +600,11 @@ def adjoint_bench(args):
         "rhs_adjoint": {"ms": ms_rhs_adj / 20, "value": nodes / (ms_rhs_adj / 20 * 1e-3),
                         "note": "includes the forward recomputation of the right-hand side"},
         "grad_norms": {"W0": float(Wbar.norm()), "b": float(bbar.norm())},
+        "autotune": {"volume_threads_per_block": tuned[0], "update_warps_per_block": tuned[1],
+                     "default": [128, 4],
+                     "plain_forward_ms_per_step": {"default": ms_plain / T, "tuned": ms_plain_t / T},
+                     "rhs_ms": {"default": ms_rhs / 20, "tuned": ms_rhs_t / 20},
+                     "note": "swe_autotune on this mesh's state; every shape computes bitwise the same"},
         "large": {"workload": f"dam_break N=7 256x256 ({big.nodes} nodes), ES+AV",
                   "rhs_ms": ms_big / 5, "rhs_adjoint_ms": ms_big_adj / 5,
                   "rhs_value": big.nodes / (ms_big / 5 * 1e-3),
