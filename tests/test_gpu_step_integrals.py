@@ -139,11 +139,15 @@ def test_async_failed_step_rolls_back_on_the_device():
     assert o2[5] == 0.0
 
 
-def test_async_step_replays_in_a_cuda_graph():
+@pytest.mark.parametrize("N,K1", [(3, 12), (7, 128)])
+def test_async_step_replays_in_a_cuda_graph(N, K1):
     """Captured once, replayed three times: the same bits as three
-    swe_step calls (adaptive step sizes computed on the device)."""
+    swe_step calls (adaptive step sizes computed on the device). At N = 7 on
+    128 x 128 quads (2^20 nodes) the context runs its indicator, start-state
+    copy and time step on its second stream, which the capture takes in
+    through the fork and join events."""
     swedg = swe_mod()
-    p = I.dam_break(N=3, K1=12)
+    p = I.dam_break(N=N, K1=K1)
     kw = dict(flux=1, av=True, eps0=0.025, limiter=True, rk=0, cfl=0.5)
     c = swedg.SweContext.from_problem(p, **kw)
     Wr = dev(p.W)
