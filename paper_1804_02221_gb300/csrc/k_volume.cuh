@@ -32,8 +32,9 @@
 //    forms the source term h srcx and the end takes one product less per
 //    momentum component.
 //  * One thread per element line: it runs its xi-line, hands the results
-//    over (through shared memory, or at N = 7 by a transpose across the
-//    element's eight lanes with warp shuffles, pressure sums included), then
+//    over (through shared memory, or at N = 3 and 7 by a transpose across
+//    the element's lanes with warp shuffles, at N = 7 pressure sums
+//    included), then
 //    runs the eta-line with the same index starting from them, and finishes
 //    the nodes of that column (interface lifts, viscous terms, source,
 //    scaling by -1/(w_i w_j J)) in registers.
@@ -117,14 +118,12 @@ constexpr bool vol_fits() {
     return vol_smem<N, AV, TPB>() <= 227 * 1024;
 }
 
-// Blocks per SM that the shared memory admits (228 KB per SM, 1 KB reserved
-// per block), passed to __launch_bounds__ so that the register allocation
-// does not lower the occupancy below what the staging allows.
-// The bound is the block count that the staging of the shared-memory
-// hand-over (all F_COUNT planes) admits, also where the shuffle hand-over
-// stages fewer planes: the shuffle variants keep the registers of the pair
-// loops (168 a thread at N = 7; capping them to the blocks the smaller
-// staging admits spills).
+// Blocks per SM passed to __launch_bounds__: the count that the staging of
+// the shared-memory hand-over (all F_COUNT planes; 228 KB per SM, 1 KB
+// reserved per block) admits, so that the register allocation does not
+// lower the occupancy below it. The shuffle variants stage fewer planes but
+// keep this bound and with it the registers of the pair loops (168 a thread
+// at N = 7; capping them to the blocks the smaller staging admits spills).
 template <int N, bool AV, int TPB>
 constexpr int vol_min_blocks() {
     constexpr int threads = vol_ne<N, TPB>() * (N + 1);
@@ -183,7 +182,8 @@ __device__ __forceinline__ void pair_loop(const double* __restrict__ s, int base
         const int ni = base + i * stride;
         const double hu_i = sHU[ni], hv_i = sHV[ni], u_i = sU[ni], v_i = sV[ni];
         const double h_i = sH[ni];
-        // 2g h_i (the per-pair pressure; the plane is absent with the shuffle hand-over)
+        // 2g h_i for the per-pair pressure (degrees without the pressure
+        // sums; with them the plane may be absent, as at N = 7)
         double p_i = 0.0;
         if constexpr (!vol_pressure_sums<N>()) p_i = sP[ni];
 #pragma unroll
@@ -362,7 +362,9 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         if constexpr (vol_pressure_sums<N>()) {
 #pragma unroll
             for (int p = 0; p < n; ++p) {
-                const double pp = vol_shfl<N>() ? g2 * S(F_H)[e * nn + p * n + l] : S(F_P)[e * nn + p * n + l];
+                double pp;  // 2g h of the node
+                if constexpr (vol_planes<N>() > (int)F_P) pp = S(F_P)[e * nn + p * n + l];
+                else pp = g2 * S(F_H)[e * nn + p * n + l];
                 A2[p] = fma(pp, B2[p], A2[p]);
                 A3[p] = fma(pp, B3[p], A3[p]);
             }
