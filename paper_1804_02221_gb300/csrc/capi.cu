@@ -159,7 +159,7 @@ int create_ctx(int N, int K, const double* x, const double* y, const int32_t* ET
         cfln(KN), rvol(K), Jv(KN);
     // the source as the start of the split volume kernel's pressure sums
     // (degrees with pressure sums only; empty otherwise)
-    const bool psums = p->volume == 0 && N >= 5;
+    const bool psums = p->volume == 0 && swe::pressure_sums_degree(N);
     std::vector<double> ssx(psums ? KN : 0), ssy(psums ? KN : 0);
     std::vector<double> tmp(4 * nn);
     for (int k = 0; k < K; ++k) {

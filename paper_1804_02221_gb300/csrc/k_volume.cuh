@@ -82,7 +82,7 @@ constexpr int vol_ne() {
 // (measured; at N = 3 the per-node products cost more than the pairs save).
 template <int N>
 constexpr bool vol_pressure_sums() {
-    return N >= 5;
+    return pressure_sums_degree(N);
 }
 
 // The xi -> eta hand-over through warp shuffles. Where n = N + 1 is a power

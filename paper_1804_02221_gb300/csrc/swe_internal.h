@@ -68,6 +68,13 @@ enum KernelClass {
     KC_COUNT = 10
 };
 
+// Degrees whose split-form volume kernel sums the pressure parts of the
+// pair fluxes per node and starts those sums from the bathymetry source (the
+// host stores the source as DeviceMesh::ssx, ssy for them).
+constexpr bool pressure_sums_degree(int N) {
+    return N >= 3;
+}
+
 // Device-side data of one context. Nodal arrays are [K][n][n] planes,
 // side arrays [K][4][n] (element side node), face arrays [nfaces][n].
 struct DeviceMesh {
