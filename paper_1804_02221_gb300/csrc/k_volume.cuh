@@ -25,12 +25,12 @@
 //    v A1), and the mass row 2 A1 is scaled by 2f = -2/(w_i w_j J) instead
 //    of doubling A1. One pair is then 15 FP64 instructions (4 for Q,
 //    1 for P, 2 for the mass sums, 8 fused multiply-adds for the momenta).
-//    From N = 5 up the pressure parts P Sx = p_i (h_q Sx) are summed per
-//    node as h_q Sx (B2, B3) and scaled by the node's p = 2g h once per line:
-//    14 per pair. The eta-line sums start from w_i w_j gamma / 4 (the split
-//    bathymetry source, sum_q b_q Sx over both lines), so the scaling also
-//    forms the source term h srcx and the end takes one product less per
-//    momentum component.
+//    From N = 3 up the pressure parts P Sx = p_i (h_q Sx) are summed per
+//    node as h_q Sx (B2, B3) and scaled by the node's p = 2g h once per line
+//    (once per node with the shuffle hand-over): 14 per pair. The sums start
+//    from w_i w_j gamma / 4 (the split bathymetry source, sum_q b_q Sx over
+//    both lines), so the scaling also forms the source term h srcx and the
+//    end takes one product less per momentum component.
 //  * One thread per element line: it runs its xi-line, hands the results
 //    over (through shared memory, or at N = 3 and 7 by a transpose across
 //    the element's lanes with warp shuffles, at N = 7 pressure sums
@@ -78,8 +78,10 @@ constexpr int vol_ne() {
 }
 
 // Pressure parts of the pair fluxes summed per node (14 FP64 instructions
-// per pair and 4 per node instead of 15 per pair): a gain from N = 5 up
-// (measured; at N = 3 the per-node products cost more than the pairs save).
+// per pair and 2 or 4 per node instead of 15 per pair), the sums started from
+// the source (2 per node fewer at the end): a gain from N = 3 up (measured:
+// N = 3 -5%, N = 4 -3%, N = 5, 6, 8 -3%; without the source in the sums the
+// per-node products cost what the pairs save at N = 3).
 template <int N>
 constexpr bool vol_pressure_sums() {
     return pressure_sums_degree(N);
@@ -447,8 +449,10 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
 // then adds the own-velocity parts, the interface lifts (tangential weight
 // times F_out, every side), the viscous terms and the source, and scales by
 // -1/(w_i w_j J): no shared memory and no barriers. The arithmetic of a pair
-// is the line kernel's (15 FP64 instructions); the block size (TPB elements)
-// is the launch shape, with the same instructions for every shape.
+// is the line kernel's with pressure sums (14 FP64 instructions; the sums of
+// both lines start from the source and are scaled by 2g h once per node, the
+// mass row by the stored 2f); the block size (TPB elements) is the launch
+// shape, with the same instructions for every shape.
 template <int N>
 constexpr bool vol_ept() {
     return N <= 1;
@@ -461,6 +465,7 @@ __device__ __forceinline__ int side_node(int f, int p) {
 
 template <int N, bool AV, int TPB>
 __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
+    static_assert(pressure_sums_degree(N), "the element-per-thread kernel starts its pressure sums from ssx");
     constexpr int n = N + 1, nn = n * n, NP = N * (N + 1) / 2;
     if (stopped(a.stop)) return;
     const DeviceMesh& m = a.m;
@@ -468,7 +473,10 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
     if (k >= m.K) return;
     const long long g0 = k * nn;
     const double g2 = 2.0 * m.g;
-    double h[nn], hu[nn], hv[nn], u[nn], v[nn], pp[nn], A1[nn], A2[nn], A3[nn];
+    // B2, B3: the pressure sums sum_q h_q Sx, h_q Sy of both lines of a node,
+    // started from the bathymetry source w_i w_j gamma / 4 and scaled by the
+    // node's 2g h once, after all pairs (the line kernel's pressure sums)
+    double h[nn], hu[nn], hv[nn], u[nn], v[nn], A1[nn], A2[nn], A3[nn], B2[nn], B3[nn];
 #pragma unroll
     for (int d = 0; d < nn; ++d) {
         h[d] = a.W[g0 + d];
@@ -476,8 +484,9 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
         hv[d] = a.W[2 * m.KN + g0 + d];
         u[d] = a.uv[g0 + d];
         v[d] = a.uv[m.KN + g0 + d];
-        pp[d] = g2 * h[d];
         A1[d] = A2[d] = A3[d] = 0.0;
+        B2[d] = m.ssx[g0 + d];
+        B3[d] = m.ssy[g0 + d];
     }
     // pair constants of the element: [direction][pair][line][2]
     const double* pm = m.pm + (size_t)k * 4 * NP * n;
@@ -495,23 +504,30 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
                     const double2 c =
                         __ldg(reinterpret_cast<const double2*>(pm + 2 * ((dir * NP + pr) * n + l)));
                     const double Q = fma(hu[ni] + hu[nq], c.x, (hv[ni] + hv[nq]) * c.y);
-                    const double P = pp[ni] * h[nq];
                     A1[ni] += Q;
                     A1[nq] -= Q;
-                    A2[ni] = fma(P, c.x, fma(u[nq], Q, A2[ni]));
-                    A2[nq] = fma(-P, c.x, fma(-u[ni], Q, A2[nq]));
-                    A3[ni] = fma(P, c.y, fma(v[nq], Q, A3[ni]));
-                    A3[nq] = fma(-P, c.y, fma(-v[ni], Q, A3[nq]));
+                    A2[ni] = fma(u[nq], Q, A2[ni]);
+                    A2[nq] = fma(-u[ni], Q, A2[nq]);
+                    A3[ni] = fma(v[nq], Q, A3[ni]);
+                    A3[nq] = fma(-v[ni], Q, A3[nq]);
+                    B2[ni] = fma(h[nq], c.x, B2[ni]);
+                    B2[nq] = fma(-h[ni], c.x, B2[nq]);
+                    B3[ni] = fma(h[nq], c.y, B3[ni]);
+                    B3[nq] = fma(-h[ni], c.y, B3[nq]);
                 }
             }
         }
     }
-    // own-velocity parts of the momentum fluxes, then the mass flux 2 sum Q
+    // pressure parts (with the source) and own-velocity parts of the momentum
+    // fluxes; A1 keeps sum Q (half the mass flux difference): the mass row is
+    // scaled by 2f and its lifts take half weights (bit for bit f (2 A1 + w F))
 #pragma unroll
     for (int d = 0; d < nn; ++d) {
+        const double pp = g2 * h[d];
+        A2[d] = fma(pp, B2[d], A2[d]);
+        A3[d] = fma(pp, B3[d], A3[d]);
         A2[d] = fma(u[d], A1[d], A2[d]);
         A3[d] = fma(v[d], A1[d], A3[d]);
-        A1[d] += A1[d];
     }
     // interface flux: w_i w_j (1/w_0) F_out = (tangential weight) F_out
     const long long side = k * 4 * n;
@@ -522,7 +538,7 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
             const int d = side_node<N>(f, p);
             const long long sl = side + f * n + p;
             const double wt = wq<N>(p);
-            A1[d] = fma(wt, a.Fout[sl], A1[d]);
+            A1[d] = fma(0.5 * wt, a.Fout[sl], A1[d]);
             A2[d] = fma(wt, a.Fout[m.KS + sl], A2[d]);
             A3[d] = fma(wt, a.Fout[2 * m.KS + sl], A3[d]);
         }
@@ -567,9 +583,9 @@ __global__ void __launch_bounds__(TPB) k_volume_ept(VolArgs a) {
     for (int d = 0; d < nn; ++d) {
         const long long gid = g0 + d;
         const double f = m.fwJ[gid];
-        a.R[gid] = f * A1[d];
-        a.R[m.KN + gid] = fma(h[d], m.srcx[gid], f * A2[d]);
-        a.R[2 * m.KN + gid] = fma(h[d], m.srcy[gid], f * A3[d]);
+        a.R[gid] = m.fwJ2[gid] * A1[d];
+        a.R[m.KN + gid] = f * A2[d];
+        a.R[2 * m.KN + gid] = f * A3[d];
     }
 }
 

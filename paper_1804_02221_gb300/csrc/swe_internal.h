@@ -72,7 +72,7 @@ enum KernelClass {
 // pair fluxes per node and starts those sums from the bathymetry source (the
 // host stores the source as DeviceMesh::ssx, ssy for them).
 constexpr bool pressure_sums_degree(int N) {
-    return N >= 3;
+    return N == 1 || N >= 3;
 }
 
 // Device-side data of one context. Nodal arrays are [K][n][n] planes,
@@ -99,7 +99,7 @@ struct DeviceMesh {
     const double* fwJ;  // -1 / (w_i w_j J)
     const double* fwJ2; // -2 / (w_i w_j J) (the split volume kernel's mass row; empty otherwise)
     const double* ssx;  // w_i w_j gamma_x / 4: h srcx = -(2g h) ssx / (w_i w_j J) (the split
-    const double* ssy;  //   volume kernel's pressure sums from N = 5 up; empty otherwise)
+    const double* ssy;  //   volume kernel's pressure sums, pressure_sums_degree; empty otherwise)
     // Pair constants of the volume kernel, [K][2 directions][N(N+1)/2 pairs][n lines][2]:
     // w_i w_j D_iq / 4 * (a_i + a_q) for the pair (i, q), i < q, of each line; the
     // two components of a line are adjacent (one 16-byte load).
