@@ -100,12 +100,48 @@ constexpr bool vol_shfl() {
     return ((N + 1) & N) == 0 && N + 1 <= 32;
 }
 
-// Shared-memory planes: the staged state, 2g h where the pairs form the
-// pressure, and the hand-over planes where the hand-over goes through
-// shared memory.
+// The pressure sums handed over unscaled through two more shared-memory
+// planes (the 2g h plane's slot, F_B2, and one after the hand-over planes,
+// F_B3) and scaled once per node after the eta-line (2 FP64 instructions per
+// node fewer), where that staging admits as many 128-thread blocks per SM as
+// the one with 2g h and the 256-thread shape still fits the 227 KB a block
+// may use: N = 6, 8, 9, 10 (measured: -0.7 to -1.9% of the kernel). Decided
+// per degree, not per launch shape, so that every shape computes the same
+// bits.
+enum { F_B2 = F_P, F_B3 = F_COUNT };
+template <int N>
+constexpr bool vol_bhand() {
+    if constexpr (!vol_pressure_sums<N>() || vol_shfl<N>()) {
+        return false;
+    } else {
+        constexpr size_t plane = sizeof(double) * (size_t)vol_ne<N, 128>() * (N + 1) * (N + 1);
+        constexpr size_t wide = sizeof(double) * (size_t)vol_ne<N, 256>() * (N + 1) * (N + 1);
+        return (228 * 1024) / (F_COUNT * plane + 1024) == (228 * 1024) / ((F_COUNT + 1) * plane + 1024) &&
+               (F_COUNT + 1) * wide <= 227 * 1024;
+    }
+}
+
+// The pressure sums run through both lines unscaled (started from the
+// source in the xi-line) and are scaled by 2g h once per node.
+template <int N>
+constexpr bool vol_unscaled() {
+    return vol_pressure_sums<N>() && (vol_shfl<N>() || vol_bhand<N>());
+}
+
+// The 2g h plane: where the pairs form the pressure, or where the sums are
+// scaled once per line.
+template <int N>
+constexpr bool vol_has_p() {
+    return !vol_pressure_sums<N>() || !vol_unscaled<N>();
+}
+
+// Shared-memory planes: the staged state, 2g h (vol_has_p), and the
+// hand-over planes where the hand-over goes through shared memory (with
+// the two pressure-sum planes for vol_bhand).
 template <int N>
 constexpr int vol_planes() {
-    return vol_shfl<N>() ? (vol_pressure_sums<N>() ? (int)F_P : (int)F_P + 1) : (int)F_COUNT;
+    return vol_shfl<N>() ? (vol_has_p<N>() ? (int)F_P + 1 : (int)F_P)
+                         : (vol_bhand<N>() ? (int)F_COUNT + 1 : (int)F_COUNT);
 }
 
 template <int N, bool AV, int TPB>
@@ -251,7 +287,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
         S(F_HV)[idx] = hv;
         S(F_U)[idx] = u;
         S(F_V)[idx] = v;
-        if constexpr (vol_planes<N>() > (int)F_P) S(F_P)[idx] = g2 * h;
+        if constexpr (vol_has_p<N>()) S(F_P)[idx] = g2 * h;
     }
     __syncthreads();
 
@@ -275,7 +311,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
 #pragma unroll
     for (int p = 0; p < n; ++p) A1[p] = A2[p] = A3[p] = B2[p] = B3[p] = 0.0;
     if (valid) {
-        if constexpr (vol_shfl<N>() && vol_pressure_sums<N>()) {
+        if constexpr (vol_unscaled<N>()) {
             // the pressure sums start from the source (see the eta-line)
             // and run through both lines before they are scaled
 #pragma unroll
@@ -285,7 +321,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             }
         }
         pair_loop<N, BLK>(sm, e * nn + l * n, 1, pmx, A1, A2, A3, B2, B3);
-        if constexpr (vol_pressure_sums<N>() && !vol_shfl<N>()) {
+        if constexpr (vol_pressure_sums<N>() && !vol_unscaled<N>()) {
             // the pressure parts P Sx = 2g h_i h_q Sx: the node's 2g h times its sums
 #pragma unroll
             for (int p = 0; p < n; ++p) {
@@ -339,6 +375,10 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             S(F_A1)[e * nn + l * n + p] = A1[p];
             S(F_A2)[e * nn + l * n + p] = A2[p];
             S(F_A3)[e * nn + l * n + p] = A3[p];
+            if constexpr (vol_bhand<N>()) {
+                S(F_B2)[e * nn + l * n + p] = B2[p];
+                S(F_B3)[e * nn + l * n + p] = B3[p];
+            }
         }
         __syncthreads();
 #pragma unroll
@@ -346,12 +386,16 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
             A1[p] = S(F_A1)[e * nn + p * n + l];
             A2[p] = S(F_A2)[e * nn + p * n + l];
             A3[p] = S(F_A3)[e * nn + p * n + l];
+            if constexpr (vol_bhand<N>()) {
+                B2[p] = S(F_B2)[e * nn + p * n + l];
+                B3[p] = S(F_B3)[e * nn + p * n + l];
+            }
         }
     }
 
     // ---- eta-line i = l, starting from the xi results ----------------------
     if (valid) {
-        if constexpr (vol_pressure_sums<N>() && !vol_shfl<N>()) {
+        if constexpr (vol_pressure_sums<N>() && !vol_unscaled<N>()) {
             // the eta-line pressure sums start from the source: 2g h ssx
             // scaled by f is the source term h srcx of the node
 #pragma unroll
@@ -365,7 +409,7 @@ __global__ void __launch_bounds__(vol_ne<N, TPB>() * (N + 1), (vol_min_blocks<N,
 #pragma unroll
             for (int p = 0; p < n; ++p) {
                 double pp;  // 2g h of the node
-                if constexpr (vol_planes<N>() > (int)F_P) pp = S(F_P)[e * nn + p * n + l];
+                if constexpr (vol_has_p<N>()) pp = S(F_P)[e * nn + p * n + l];
                 else pp = g2 * S(F_H)[e * nn + p * n + l];
                 A2[p] = fma(pp, B2[p], A2[p]);
                 A3[p] = fma(pp, B3[p], A3[p]);
