@@ -104,10 +104,12 @@ constexpr bool vol_shfl() {
 // planes (the 2g h plane's slot, F_B2, and one after the hand-over planes,
 // F_B3) and scaled once per node after the eta-line (2 FP64 instructions per
 // node fewer), where that staging admits as many 128-thread blocks per SM as
-// the one with 2g h and the 256-thread shape still fits the 227 KB a block
-// may use: N = 6, 8, 9, 10 (measured: -0.7 to -1.9% of the kernel). Decided
-// per degree, not per launch shape, so that every shape computes the same
-// bits.
+// the one with 2g h, or at least three (12 warps, the N = 7 kernel's), and
+// the 256-thread shape still fits the 227 KB a block may use: N = 2, 4, 5, 6,
+// 8, 9, 10 (measured: -0.7 to -2.6% of the kernel, also where a block per SM
+// is lost: N = 4 and 5 gain from the registers the lower count allows).
+// Decided per degree, not per launch shape, so that every shape computes the
+// same bits.
 enum { F_B2 = F_P, F_B3 = F_COUNT };
 template <int N>
 constexpr bool vol_bhand() {
@@ -116,7 +118,8 @@ constexpr bool vol_bhand() {
     } else {
         constexpr size_t plane = sizeof(double) * (size_t)vol_ne<N, 128>() * (N + 1) * (N + 1);
         constexpr size_t wide = sizeof(double) * (size_t)vol_ne<N, 256>() * (N + 1) * (N + 1);
-        return (228 * 1024) / (F_COUNT * plane + 1024) == (228 * 1024) / ((F_COUNT + 1) * plane + 1024) &&
+        constexpr size_t blocks = (228 * 1024) / ((F_COUNT + 1) * plane + 1024);
+        return (blocks == (228 * 1024) / (F_COUNT * plane + 1024) || blocks >= 3) &&
                (F_COUNT + 1) * wide <= 227 * 1024;
     }
 }
@@ -157,16 +160,18 @@ constexpr bool vol_fits() {
 }
 
 // Blocks per SM passed to __launch_bounds__: the count that the staging of
-// the shared-memory hand-over (all F_COUNT planes; 228 KB per SM, 1 KB
-// reserved per block) admits, so that the register allocation does not
-// lower the occupancy below it. The shuffle variants stage fewer planes but
-// keep this bound and with it the registers of the pair loops (168 a thread
-// at N = 7; capping them to the blocks the smaller staging admits spills).
+// the shared-memory hand-over (all F_COUNT planes, one more with vol_bhand;
+// 228 KB per SM, 1 KB reserved per block) admits, so that the register
+// allocation does not lower the occupancy below it. The shuffle variants
+// stage fewer planes but keep this bound and with it the registers of the
+// pair loops (168 a thread at N = 7; capping them to the blocks the smaller
+// staging admits spills).
 template <int N, bool AV, int TPB>
 constexpr int vol_min_blocks() {
     constexpr int threads = vol_ne<N, TPB>() * (N + 1);
     constexpr int warps = (threads + 31) / 32;
-    constexpr size_t full = sizeof(double) * ((size_t)F_COUNT * vol_ne<N, TPB>() * (N + 1) * (N + 1));
+    constexpr size_t full =
+        sizeof(double) * ((size_t)(vol_bhand<N>() ? F_COUNT + 1 : F_COUNT) * vol_ne<N, TPB>() * (N + 1) * (N + 1));
     constexpr int by_smem = (int)((228 * 1024) / (full + 1024));
     constexpr int by_warps = 64 / warps;
     constexpr int b = by_smem < by_warps ? by_smem : by_warps;

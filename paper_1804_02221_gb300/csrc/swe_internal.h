@@ -72,7 +72,7 @@ enum KernelClass {
 // pair fluxes per node and starts those sums from the bathymetry source (the
 // host stores the source as DeviceMesh::ssx, ssy for them).
 constexpr bool pressure_sums_degree(int N) {
-    return N == 1 || N >= 3;
+    return N >= 1;
 }
 
 // Device-side data of one context. Nodal arrays are [K][n][n] planes,
