@@ -24,7 +24,14 @@
  * the geometry and the scratch buffers it allocates on the device at
  * swe_create and releases at swe_destroy. Device pointers must stay valid
  * while work queued on the given stream runs. A NULL stream is the legacy
- * default stream.
+ * default stream. A context's scratch buffers serve one call at a time:
+ * calls on one context that may overlap on the GPU (different streams, or
+ * different host threads) must be serialised by the caller. A context of at
+ * least 2^20 nodes also owns a second stream: parts of a right-hand side and
+ * of a step (the smoothness indicator, a step's start-state copy and time
+ * step) run there beside the interface flux, forked from and joined back into
+ * the caller's stream by events, so the caller's stream order holds and the
+ * calls stay capturable in a CUDA graph.
  *
  * Errors: every int-returning call returns SWE_OK (0) or a negative code; the
  * text of the last error of the calling thread is swe_last_error(). No call
