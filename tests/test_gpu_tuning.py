@@ -23,7 +23,7 @@ def dev(W):
     return torch.from_numpy(np.ascontiguousarray(W)).cuda()
 
 
-@pytest.mark.parametrize("N,K1", [(1, 9), (3, 7), (5, 5), (7, 5), (11, 2)])
+@pytest.mark.parametrize("N,K1", [(1, 9), (2, 8), (3, 7), (5, 5), (7, 5), (8, 3), (11, 2)])
 def test_every_shape_is_bitwise_identical(N, K1):
     p = I.random_rough(N=N, K1=K1, seed=40 + N, dry_fraction=0.05)
     swedg = swe_mod()
